@@ -1,0 +1,404 @@
+"""Benchmark: photon packets/s of the SDF Monte Carlo transport path.
+
+Workload (one "step"): the three-layer slab -- three box SDF layers 0.1 /
+0.2 / 1.0 cm thick (mu_a 0.1-2, mu_s 10-100 /cm, g 0.8-0.95, n 1.3-1.5),
+pencil beam, 1e7 packets, 100^3 int64 fluence grid -- in the mixed
+precision mode (FP32 tracing, FP64 interface refinement).  ``value`` is
+packets/s with the scene resident on the device; the JSON line also carries
+the plain-FP64 mode on the same workload, R/T/A against the FP64 CPU
+oracle, the served mix's p50/p99 job latency, the roofline of the packet
+kernel, and the oracle timed on the host cores.
+
+Multi-GPU (torchrun): packets are independent, so each rank runs its own
+1e7-packet block of ids (weak scaling, no data-path collective); the step
+time is the max over ranks.
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "photon packets/s (and p50/p99 job latency) mixed vs plain FP64 at equal R/T/A error"
+UNIT = "packets/s"
+FX = 2.0 ** 32
+
+# Algorithmic FP32 work per counted event of the mixed kernel (operations,
+# an FMA counted as 2), from the arithmetic of the kernel source:
+#   box SDF 22 (3 sub, 3 abs, 3 sub, 3 max, 5 for the squared norm, sqrt,
+#   3 min/max, add); region bookkeeping 5 per region (compare, abs, compare,
+#   2 selects); bounding box = one box SDF;
+#   step: tally set-up 40 + move 6 + tau update 2;  voxel piece 16;
+#   interaction: weight 3, HG 12, azimuth sincos 4, basis 14, rotation 15,
+#   normalisation 8, roulette 2, log 4 = 62.
+FLOPS_BOX = 22
+FLOPS_REGION = 5
+FLOPS_STEP = 48
+FLOPS_PIECE = 16
+FLOPS_INTERACTION = 62
+
+
+def three_layer_flops(t: dict) -> float:
+    per_eval = 3 * FLOPS_BOX + 3 * FLOPS_REGION + FLOPS_BOX
+    return (t["scene_evals"] * per_eval + t["steps"] * FLOPS_STEP + t["pieces"] * FLOPS_PIECE
+            + t["scatters"] * FLOPS_INTERACTION)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def oracle_sample(wl, seconds: float, id_base: int = 0):
+    """Time the FP64 oracle, as it stands, on a bounded sample sized to take
+    about ``seconds``; returns (packets/s, packets, threads, totals)."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    n0 = 2000
+    t0 = time.perf_counter()
+    O.run(wl.with_packets(n0), id_base, id_base + n0, threads=threads, fluence=True)
+    rate0 = n0 / (time.perf_counter() - t0)
+    n = int(max(n0, min(5_000_000, rate0 * seconds)))
+    t0 = time.perf_counter()
+    _, tot, rec = O.run(wl.with_packets(n), id_base, id_base + n, threads=threads, records=True)
+    dt = time.perf_counter() - t0
+    return n / dt, n, threads, tot, rec
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = W.three_layer_slab(precision="fp64")
+    import oracle as O
+    O.build()
+    threads = os.cpu_count() or 1
+    # a bounded sample per step: about 8 s of oracle work each
+    n0 = 2000
+    t0 = time.perf_counter()
+    O.run(wl.with_packets(n0), 0, n0, threads=threads)
+    rate0 = n0 / (time.perf_counter() - t0)
+    n = int(max(n0, rate0 * 8.0))
+    for i in range(args.warmup):
+        O.run(wl.with_packets(min(n, 4000)), 0, min(n, 4000), threads=threads)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        O.run(wl.with_packets(n), i * n, (i + 1) * n, threads=threads)
+        times.append(time.perf_counter() - t0)
+    value = n * args.steps / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "three_layer_slab (1e7 packets, 100^3 grid), sampled",
+                       "sample_packets_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} packets of three_layer_slab per step (ids disjoint per step)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def served_mix(ctx, njobs: int, capacity_pps: float, load: float = 0.8, seed: int = 4):
+    """Poisson arrivals of the served mix at ``load`` x measured capacity;
+    returns latencies and served throughput."""
+    jobs = W.served_mix(njobs, seed)
+    total = sum(j.npackets for j in jobs)
+    rng = np.random.default_rng(seed)
+    mean_gap = (total / njobs) / (capacity_pps * load)
+    arrivals = np.cumsum(rng.exponential(mean_gap, njobs))
+    ids, lat = [], []
+    t0 = time.perf_counter()
+    done = threading.Event()
+    pending = []
+    lock = threading.Lock()
+
+    def waiter():
+        while True:
+            with lock:
+                item = pending.pop(0) if pending else None
+            if item is None:
+                if done.is_set():
+                    return
+                time.sleep(0.0005)
+                continue
+            _, tot, l = ctx.wait(item, -1.0, fluence=False)
+            lat.append(l)
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    for j, wl in enumerate(jobs):
+        delay = arrivals[j] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        jid = ctx.submit(wl, "mixed")
+        with lock:
+            pending.append(jid)
+        ids.append(jid)
+    done.set()
+    th.join()
+    wall = time.perf_counter() - t0
+    lat_ms = np.array(lat) * 1e3
+    return {"jobs": njobs, "packets": int(total), "wall_s": wall, "served_pps": total / wall,
+            "offered_load": load, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean())}
+
+
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--packets", type=int, default=10_000_000)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--serve-jobs", type=int, default=100)
+    ap.add_argument("--oracle-seconds", type=float, default=15.0)
+    ap.add_argument("--quick", action="store_true", help="kernel legs only (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_2112_08035_gb300 as smc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    ctx = smc.Context(local)
+    wl = W.three_layer_slab(args.packets, precision="mixed")
+    g = wl.grid
+    id0 = rank * args.packets
+    plan = ctx.plan(wl, "mixed")
+    flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
+    tot = smc.totals_tensor()
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(p, precision_plan, seed, first_id):
+        flu.zero_()
+        tot.zero_()
+        precision_plan.launch(first_id, p, seed, flu, tot, None, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step(args.packets, plan, wl.seed, id0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        for i in range(args.steps):
+            l2_flush.fill_(float(i))      # L2 flush between timed iterations (not timed)
+            ev[i][0].record(stream)
+            step(args.packets, plan, wl.seed, id0)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    step_s = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    t_sum = sum(step_s)
+    if dist:
+        tt = torch.tensor([t_sum], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_sum = float(tt.item())
+    totals_mixed = smc.totals_from_tensor(tot)
+    value = args.packets * args.steps * world / t_sum
+    kernel_s = t_sum / args.steps   # per-step device time ~ the packet kernel (one launch)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed; int64 tallies)",
+           "data": "synthetic",
+           "config": {"workload": f"three_layer_slab: 3 box-SDF layers, pencil beam, {args.packets:.0e} packets "
+                                  f"per GPU, 100^3 int64 fluence grid, mixed precision",
+                      "packets_per_step": args.packets * world, "l2": "flushed between timed steps (256 MB write)"},
+           "gpu_launches": 2 * args.steps,
+           "clocks": clk.summary()}
+
+    # ---- roofline of the packet kernel (ALU-bound: FP32 issue) -----------
+    peaks, src = load_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = out["clocks"]["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1455.0
+    peak_tflops = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    flops = three_layer_flops(totals_mixed)
+    achieved = flops / kernel_s / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                       "frac": achieved / peak_tflops, "traffic": None,
+                       "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 (FMA) x {mhz:.0f} MHz "
+                                     f"(median SM clock sampled under load)",
+                       "kernel": "packets_mixed",
+                       "algorithmic_flops_per_packet": flops / args.packets,
+                       "atomics_per_s": totals_mixed["pieces"] / kernel_s}
+    out["counters_per_packet"] = {k: totals_mixed[k] / args.packets for k in
+                                  ("steps", "scene_evals", "scatters", "interfaces", "fresnel", "pieces")}
+    out["counters_per_packet"]["refined_fraction_of_fresnel"] = (
+        totals_mixed["refined"] / max(1, totals_mixed["fresnel"]))
+
+    if not args.quick:
+        # ---- plain FP64 mode on the same workload ---------------------------
+        log(f"mixed {value:.3e} packets/s; timing the FP64 mode")
+        plan64 = ctx.plan(wl, "fp64")
+        step(min(args.packets, 1_000_000), plan64, wl.seed, id0)
+        torch.cuda.synchronize()
+        e64 = []
+        for i in range(args.fp64_steps):
+            l2_flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(args.packets, plan64, wl.seed, id0)
+            b.record(stream)
+            e64.append((a, b))
+        torch.cuda.synchronize()
+        t64 = sum(a.elapsed_time(b) for a, b in e64) / 1e3 / args.fp64_steps
+        totals_fp64 = smc.totals_from_tensor(tot)
+        plan64.close()
+        out["fp64"] = {"value": args.packets / t64, "unit": UNIT, "ms_per_step": 1e3 * t64,
+                       "mixed_speedup": (args.packets / kernel_s) / (args.packets / t64)}
+
+        log(f"fp64 {args.packets / t64:.3e} packets/s; end-to-end leg")
+        # ---- end to end through the public API with host buffers -------------
+        m = smc.Marshalled(wl.scene, wl.source, wl.grid)
+        h_flu = np.zeros((g.n[2], g.n[1], g.n[0]), dtype=np.int64)
+        import ctypes as C
+        h2d = (C.sizeof(m.scene) + C.sizeof(m.prims) + C.sizeof(m.nodes) + C.sizeof(m.regions)
+               + C.sizeof(m.source) + C.sizeof(m.grid))
+        ctx.run(wl.with_packets(100_000), "mixed", out=h_flu)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_steps = 3
+        for i in range(e2e_steps):
+            _, te = ctx.run(wl, "mixed", out=h_flu)
+        e2e_t = (time.perf_counter() - t0) / e2e_steps
+        out["e2e"] = {"value": args.packets / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(h_flu.nbytes + C.sizeof(smc.Totals)),
+                      "api": "smcrt_run with host scene structs and a host fluence buffer"}
+
+        log("oracle leg")
+        # ---- accuracy against the FP64 oracle, and the oracle's CPU timing ----
+        o_pps, o_n, o_threads, o_tot, o_rec = oracle_sample(wl, args.oracle_seconds, id_base=0)
+        out["cpu_baseline"] = {"value": o_pps, "unit": UNIT, "cores": o_threads, "kind": "oracle",
+                               "sample": f"{o_n} packets (ids 0..{o_n - 1}) of the same three_layer_slab "
+                                         f"workload, FP64, {o_threads} threads"}
+        acc = {}
+        for name, t in (("mixed", totals_mixed), ("fp64", totals_fp64)):
+            d = {}
+            for k in ("R", "T", "A"):
+                ov = o_rec[k] / FX
+                sig = math.sqrt(ov.var() / ov.size + ov.var() / args.packets)
+                gv = t[k] / FX / args.packets
+                d[k] = gv
+                d[f"{k}_oracle"] = float(ov.mean())
+                d[f"{k}_z"] = (gv - float(ov.mean())) / sig
+            acc[name] = d
+        out["accuracy_vs_oracle"] = acc
+        out["accuracy_vs_oracle"]["note"] = ("GPU at 1e7 packets vs oracle sample; z = difference / combined "
+                                             "MC sigma. FP64 mode is bit-identical to the oracle packet by packet")
+
+        # ---- served mix: Poisson arrivals at 80% of measured capacity ---------
+        if args.serve_jobs > 0:
+            log("serving leg")
+            # capacity of the server on this mix: all jobs of a prefix at once
+            cap_jobs = W.served_mix(min(40, args.serve_jobs), 4)
+            t0 = time.perf_counter()
+            jids = [ctx.submit(j, "mixed") for j in cap_jobs]
+            for jid in jids:
+                ctx.wait(jid, -1.0, fluence=False)
+            cap = sum(j.npackets for j in cap_jobs) / (time.perf_counter() - t0)
+            out["serving"] = served_mix(ctx, args.serve_jobs, capacity_pps=cap)
+            out["serving"]["capacity_pps"] = cap
+    plan.close()
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

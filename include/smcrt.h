@@ -1,0 +1,277 @@
+/*
+ * smcrt.h -- C-ABI of the GB300 photon-packet propagation library.
+ *
+ * The library propagates photon packets through turbid media whose geometry
+ * is a set of signed distance functions (SDFs) combined by constructive
+ * solid geometry (CSG), as in signedMCRT (McMillan, Bruce & Dholakia,
+ * "Meshless Monte Carlo Radiation Transfer Method for Curved Geometries
+ * using Signed Distance Functions"):
+ *   - Sec. 2.1, Eq. 1: optical depth tau = -ln(xi), free path tau / mu_t;
+ *   - Sec. 2.2, Eq. 2-3 and Fig. 1: SDF primitives and CSG operations;
+ *   - Sec. 2.3, Fig. 2 (right) and Fig. 3: sphere tracing to the nearest
+ *     surface, threshold delta, Fresnel reflection / Snell refraction with
+ *     the normal from the SDF gradient, bounding box as volume of interest;
+ *   - Sec. 3.1: Henyey-Greenstein scattering; absorption weighting with
+ *     Russian roulette (the paper reuses its earlier codes' routines);
+ *   - Sec. 3.2: fluence tallied in rectangular voxel bins.
+ *
+ * Units: lengths in cm, coefficients in cm^-1.  Every tally is a signed
+ * 64-bit fixed-point number in units of 2^-32 packet weight (fluence: weight
+ * x path length in cm), accumulated with integer atomics, so results do not
+ * depend on execution order and are bit-reproducible.
+ *
+ * Conventions for every function:
+ *   - return value: SMCRT_OK (0) or a negative SMCRT_ERR_* code; on error
+ *     no output is written and no job is created;
+ *   - host structs passed in are read during the call only; the caller
+ *     keeps ownership;
+ *   - "device pointer" means memory of the context's CUDA device (for
+ *     example a torch CUDA tensor's data_ptr()); "host or device" pointers
+ *     are classified with cudaPointerGetAttributes;
+ *   - a context is used from one host thread at a time, except that
+ *     smcrt_submit / smcrt_poll / smcrt_wait / smcrt_cancel may be called
+ *     from any thread (the serving queue is internally locked).
+ */
+#ifndef SMCRT_H
+#define SMCRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SMCRT_OK 0
+#define SMCRT_ERR_BAD_ARG -1      /* null pointer, zero size, unknown enum */
+#define SMCRT_ERR_BAD_SCENE -2    /* scene / source / grid failed validation */
+#define SMCRT_ERR_NO_MEMORY -3    /* device or host allocation failed, or over budget */
+#define SMCRT_ERR_CUDA -4         /* a CUDA runtime call failed */
+#define SMCRT_ERR_TIMEOUT -5      /* smcrt_wait timed out (job keeps running) */
+#define SMCRT_ERR_CANCELLED -6    /* job was cancelled */
+#define SMCRT_ERR_NOT_FOUND -7    /* unknown job id */
+#define SMCRT_ERR_DEVICE -8       /* kernel reported an error status word */
+
+/* ---- scene description (Sec. 2.2-2.3) ---------------------------------- */
+enum smcrt_prim_kind {
+    SMCRT_SPHERE = 0,   /* p = {cx, cy, cz, r}: |x - c| - r (Eq. 2-3) */
+    SMCRT_BOX = 1,      /* p = {cx, cy, cz, hx, hy, hz}: exact box distance */
+    SMCRT_CAPSULE = 2   /* p = {ax, ay, az, bx, by, bz, r}: segment distance - r */
+};
+
+enum smcrt_op {         /* postfix CSG program nodes (Sec. 2.2, Fig. 1 e-h) */
+    SMCRT_OP_PRIM = 0,          /* push primitive `prim` */
+    SMCRT_OP_UNION = 1,         /* min(a, b) */
+    SMCRT_OP_SMOOTH_UNION = 2,  /* polynomial smooth minimum with radius k > 0 */
+    SMCRT_OP_INTERSECT = 3,     /* max(a, b) */
+    SMCRT_OP_SUBTRACT = 4       /* max(a, -b): a minus b */
+};
+
+typedef struct {
+    int32_t kind;       /* enum smcrt_prim_kind */
+    int32_t reserved;   /* must be 0 */
+    double p[7];        /* parameters, see smcrt_prim_kind */
+} smcrt_prim;
+
+typedef struct {
+    int32_t op;         /* enum smcrt_op */
+    int32_t prim;       /* primitive index for SMCRT_OP_PRIM, else ignored */
+    double k;           /* smoothing radius (cm) for SMCRT_OP_SMOOTH_UNION */
+} smcrt_csg_node;
+
+/* One optical region: its SDF is the value of nodes[node_begin ..
+ * node_begin+node_count) evaluated as a postfix program (binary operators
+ * take the earlier operand as a, the later as b).  A point belongs to the
+ * highest-index region whose SDF is negative there, else to the ambient
+ * medium (mu_a = mu_s = 0, n = ambient_n).  Sec. 2.3: "Each SDF has its
+ * own set of optical properties". */
+typedef struct {
+    int32_t node_begin;
+    int32_t node_count;
+    double mu_a;        /* absorption coefficient, >= 0 */
+    double mu_s;        /* scattering coefficient, >= 0 */
+    double g;           /* Henyey-Greenstein anisotropy, in (-1, 1) */
+    double n;           /* refractive index, >= 1 */
+} smcrt_region;
+
+typedef struct {
+    const smcrt_prim *prims;       /* host array of nprims */
+    int32_t nprims;                /* 1 .. 4096 */
+    const smcrt_csg_node *nodes;   /* host array of nnodes */
+    int32_t nnodes;
+    const smcrt_region *regions;   /* host array of nregions */
+    int32_t nregions;              /* 1 .. 64; postfix stack depth <= 4 */
+    double ambient_n;              /* refractive index outside all regions */
+    double bbox_lo[3];             /* bounding box: the volume of interest; */
+    double bbox_hi[3];             /* leaving it terminates a packet (Sec. 2.3) */
+    double delta;                  /* surface threshold delta (cm), > 0 */
+    int64_t max_steps;             /* per-packet step cap (grazing guard), > 0 */
+} smcrt_scene;
+
+enum smcrt_source_kind {
+    SMCRT_SRC_PENCIL = 0,     /* all packets start at pos heading dir */
+    SMCRT_SRC_DISC = 1,       /* uniform over a disc of `radius` about pos, normal dir */
+    SMCRT_SRC_SQUARE = 2,     /* uniform over a square of half side `radius` about pos */
+    SMCRT_SRC_ISO_POINT = 3   /* isotropic directions from pos */
+};
+
+typedef struct {
+    int32_t kind;        /* enum smcrt_source_kind */
+    int32_t reserved;    /* must be 0 */
+    double pos[3];
+    double dir[3];       /* unit vector; also splits escapes into R (u.dir < 0) and T */
+    double radius;
+} smcrt_source;
+
+/* Fluence grid: n[0] x n[1] x n[2] rectangular voxels over [lo, hi],
+ * stored [z][y][x] with x fastest (Sec. 3.2 rectangular bins). */
+typedef struct {
+    double lo[3];
+    double hi[3];
+    int32_t n[3];        /* each 1 .. 1024 */
+    int32_t reserved;    /* must be 0 */
+} smcrt_grid;
+
+enum smcrt_precision {
+    SMCRT_FP64 = 0,   /* every step in FP64, bit-identical to the FP64 reference */
+    SMCRT_MIXED = 1   /* FP32 tracing/scattering; FP64 interface refinement near
+                         grazing and critical incidence; exact int64 tallies */
+};
+
+/* Totals of one run, all int64.  R, T, A, killed, gain are fixed point
+ * (2^-32 weight units): R + T + A + killed - gain = packets * 2^32 up to
+ * one half unit per deposit.  The rest are event counts. */
+typedef struct {
+    int64_t R;            /* escaped with u.dir < 0 (reflected) */
+    int64_t T;            /* escaped otherwise (transmitted) */
+    int64_t A;            /* absorbed (implicit capture, w mu_a / mu_t per interaction) */
+    int64_t killed;       /* removed by roulette or the step cap */
+    int64_t gain;         /* added by roulette survivors */
+    int64_t packets;      /* packets completed */
+    int64_t scatters;     /* interactions */
+    int64_t steps;        /* sphere-tracing iterations */
+    int64_t scene_evals;  /* full scene SDF evaluations (all phases) */
+    int64_t interfaces;   /* index-boundary arrivals (Sec. 2.3, d_sdf < delta) */
+    int64_t fresnel;      /* of which with a refractive-index change */
+    int64_t pieces;       /* voxel deposits */
+    int64_t max_steps_hit;/* packets stopped by the step cap */
+    int64_t refined;      /* mixed mode: interfaces refined in FP64 */
+    int64_t busy_cycles;  /* SM clock cycles warps spent on this job (summed over warps) */
+    int64_t reserved;
+} smcrt_totals;
+
+/* Optional per-packet record (debugging and per-packet parity). */
+typedef struct {
+    int64_t R, T, A, killed, gain, scatters, steps, reserved;
+} smcrt_packet_record;
+
+typedef struct smcrt_ctx smcrt_ctx;
+typedef struct smcrt_plan smcrt_plan;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  device_mem_budget bounds the
+ * device memory the serving queue may hold for admitted jobs (0 = 80% of
+ * the free memory at creation).  *out receives the context. */
+int smcrt_create(smcrt_ctx **out, int device, size_t device_mem_budget);
+
+/* Wait for outstanding work, free every device buffer, destroy ctx. */
+int smcrt_destroy(smcrt_ctx *ctx);
+
+/* Static string for a status code. */
+const char *smcrt_strerror(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int smcrt_version(void);
+
+/* Validate scene/source/grid and compile the CSG programs without touching
+ * a device (Sec. 2.2-2.3 scene model).  *ninstr (may be NULL) receives the
+ * length of the compiled instruction stream.  Returns OK, BAD_ARG or
+ * BAD_SCENE.  Needs no context and no GPU. */
+int smcrt_validate(const smcrt_scene *scene, const smcrt_source *source, const smcrt_grid *grid,
+                   int32_t *ninstr);
+
+/* ---- plans: a validated, compiled, device-resident scene --------------- */
+
+/* Validate scene/source/grid, compile the CSG programs into the device
+ * instruction stream of the chosen precision and upload it.  *out owns the
+ * device copy until smcrt_plan_destroy.  Errors: BAD_ARG, BAD_SCENE,
+ * NO_MEMORY, CUDA. */
+int smcrt_plan_create(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *source,
+                      const smcrt_grid *grid, int32_t precision, smcrt_plan **out);
+
+int smcrt_plan_destroy(smcrt_plan *plan);
+
+/* Launch configuration of the persistent packet kernel: blocks (0 = SM
+ * count x resident blocks per SM) and threads per block (a multiple of 32,
+ * 32 .. 128; 0 = tuned default).  Other values return BAD_ARG. */
+int smcrt_plan_set_launch(smcrt_plan *plan, int32_t blocks, int32_t threads);
+
+/* Asynchronously propagate packets [id_begin, id_begin + npackets) with
+ * Philox key `seed` on CUDA stream `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  fluence_dev (device pointer, n[0]*n[1]*n[2] int64, may
+ * be NULL for no grid tally) and totals_dev (device pointer to one
+ * smcrt_totals) are ACCUMULATED into -- zero them first for a fresh run.
+ * records_dev (device pointer to npackets records, or NULL) receives one
+ * record per packet, indexed by id - id_begin.  Packet ids are independent
+ * (counter-based RNG), so a job split into id blocks gives the same tallies
+ * as one launch. */
+int smcrt_plan_launch(smcrt_plan *plan, uint64_t id_begin, uint64_t npackets, uint64_t seed,
+                      int64_t *fluence_dev, smcrt_totals *totals_dev,
+                      smcrt_packet_record *records_dev, void *stream);
+
+/* Read back the kernel's device error word for the plan's last launches
+ * (0 = none) and clear it. */
+int smcrt_plan_status(smcrt_plan *plan, int32_t *status);
+
+/* Time the candidate launch shapes on a short trial run of this plan and
+ * keep the fastest (the choice is cached per scene shape in the context).
+ * Trial tallies go to scratch buffers.  *blocks / *threads (may be NULL)
+ * receive the choice. */
+int smcrt_plan_autotune(smcrt_plan *plan, uint64_t trial_packets, int32_t *blocks,
+                        int32_t *threads);
+
+/* ---- one-shot synchronous run ------------------------------------------ */
+
+/* Plan, launch and wait: packets [0, npackets), key `seed`.  fluence_out
+ * (host or device, n[0]*n[1]*n[2] int64, may be NULL) and totals_out (host)
+ * are OVERWRITTEN with this run's tallies.  Host-to-device and
+ * device-to-host copies happen inside the call. */
+int smcrt_run(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *source,
+              const smcrt_grid *grid, uint64_t npackets, uint64_t seed, int32_t precision,
+              int64_t *fluence_out, smcrt_totals *totals_out);
+
+/* ---- serving: continuously batched jobs ------------------------------- */
+
+/* Queue a job (same arguments as smcrt_run).  Jobs are admitted to device
+ * slots in arrival order as slots and device memory (fluence grid + scene)
+ * free up; all admitted jobs share each persistent launch, which runs
+ * under a captured CUDA graph.  *job_id receives a handle.  Errors:
+ * BAD_ARG, BAD_SCENE, NO_MEMORY (the job alone exceeds the budget). */
+int smcrt_submit(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *source,
+                 const smcrt_grid *grid, uint64_t npackets, uint64_t seed, int32_t precision,
+                 uint64_t *job_id);
+
+/* *done = 1 when the job's results are ready (or it failed), else 0. */
+int smcrt_poll(smcrt_ctx *ctx, uint64_t job_id, int32_t *done);
+
+/* Block until the job completes or timeout_s elapses (< 0: forever).
+ * Copies the fluence (host pointer, may be NULL) and totals (host, may be
+ * NULL), then releases the job.  Returns TIMEOUT (job kept), CANCELLED,
+ * DEVICE, or OK.  *latency_s (may be NULL) receives submit-to-completion
+ * wall time. */
+int smcrt_wait(smcrt_ctx *ctx, uint64_t job_id, double timeout_s, int64_t *fluence_out,
+               smcrt_totals *totals_out, double *latency_s);
+
+/* Stop issuing new packets of the job; its result becomes CANCELLED. */
+int smcrt_cancel(smcrt_ctx *ctx, uint64_t job_id);
+
+/* Serving counters: jobs queued, running, launches issued so far. */
+int smcrt_serving_stats(smcrt_ctx *ctx, int64_t *queued, int64_t *running, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMCRT_H */

@@ -1,0 +1,1110 @@
+// smcrt_api.cpp -- host runtime behind the C-ABI of include/smcrt.h:
+// validation, CSG compilation into the device instruction stream, plans,
+// the one-shot run, the launch-shape autotuner and the continuously
+// batched serving scheduler.
+//
+// Compiled as host C++ with -ffp-contract=off: the double constants it
+// precomputes for the FP64 kernel (capsule |b-a|^2, bounding-box centre and
+// half extent, mu_t, albedo, source basis, voxel size) use the expressions
+// of the FP64 reference so both see identical values.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "smcrt_internal.h"
+
+using namespace smcrt;
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+#define CU(x)                                        \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return SMCRT_ERR_CUDA; \
+    } while (0)
+
+bool finite(double x) { return std::isfinite(x); }
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+float ulp_f32(float x)
+{
+    x = std::fabs(x);
+    return std::nextafter(x, INFINITY) - x;
+}
+
+// Orthonormal basis perpendicular to unit n (Duff et al., JCGT 2017); same
+// expression order as the FP64 reference.
+void onb_host(const double n[3], double b1[3], double b2[3])
+{
+    const double sg = std::copysign(1.0, n[2]);
+    const double a = -1.0 / (sg + n[2]);
+    const double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sg * n[0] * n[0] * a;
+    b1[1] = sg * b;
+    b1[2] = -sg * n[0];
+    b2[0] = b;
+    b2[1] = sg + n[1] * n[1] * a;
+    b2[2] = -n[1];
+}
+
+int validate(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid *g)
+{
+    if (!sc || !src || !g) return SMCRT_ERR_BAD_ARG;
+    if (!sc->prims || !sc->nodes || !sc->regions) return SMCRT_ERR_BAD_ARG;
+    if (sc->nprims < 1 || sc->nprims > kMaxPrims) return SMCRT_ERR_BAD_SCENE;
+    if (sc->nregions < 1 || sc->nregions > kMaxRegions) return SMCRT_ERR_BAD_SCENE;
+    if (sc->nnodes < 1) return SMCRT_ERR_BAD_SCENE;
+    for (int i = 0; i < sc->nprims; ++i) {
+        const smcrt_prim &p = sc->prims[i];
+        for (int k = 0; k < 7; ++k)
+            if (!finite(p.p[k])) return SMCRT_ERR_BAD_SCENE;
+        if (p.kind == SMCRT_SPHERE) {
+            if (!(p.p[3] > 0)) return SMCRT_ERR_BAD_SCENE;
+        } else if (p.kind == SMCRT_BOX) {
+            if (!(p.p[3] > 0 && p.p[4] > 0 && p.p[5] > 0)) return SMCRT_ERR_BAD_SCENE;
+        } else if (p.kind == SMCRT_CAPSULE) {
+            const double dx = p.p[3] - p.p[0], dy = p.p[4] - p.p[1], dz = p.p[5] - p.p[2];
+            if (!(p.p[6] > 0) || !(dx * dx + dy * dy + dz * dz > 0)) return SMCRT_ERR_BAD_SCENE;
+        } else {
+            return SMCRT_ERR_BAD_SCENE;
+        }
+    }
+    for (int r = 0; r < sc->nregions; ++r) {
+        const smcrt_region &R = sc->regions[r];
+        if (R.node_count < 1 || R.node_begin < 0 || R.node_begin + R.node_count > sc->nnodes)
+            return SMCRT_ERR_BAD_SCENE;
+        if (!(R.mu_a >= 0 && R.mu_s >= 0 && finite(R.mu_a) && finite(R.mu_s))) return SMCRT_ERR_BAD_SCENE;
+        if (!(R.g > -1 && R.g < 1)) return SMCRT_ERR_BAD_SCENE;
+        if (!(R.n >= 1 && finite(R.n))) return SMCRT_ERR_BAD_SCENE;
+    }
+    if (!(sc->ambient_n >= 1 && finite(sc->ambient_n))) return SMCRT_ERR_BAD_SCENE;
+    for (int a = 0; a < 3; ++a)
+        if (!(sc->bbox_lo[a] < sc->bbox_hi[a]) || !finite(sc->bbox_lo[a]) || !finite(sc->bbox_hi[a]))
+            return SMCRT_ERR_BAD_SCENE;
+    if (!(sc->delta > 0 && finite(sc->delta))) return SMCRT_ERR_BAD_SCENE;
+    if (sc->max_steps < 1 || sc->max_steps > (int64_t(1) << 31)) return SMCRT_ERR_BAD_SCENE;
+    if (src->kind < SMCRT_SRC_PENCIL || src->kind > SMCRT_SRC_ISO_POINT) return SMCRT_ERR_BAD_SCENE;
+    const double dl = std::sqrt(src->dir[0] * src->dir[0] + src->dir[1] * src->dir[1] + src->dir[2] * src->dir[2]);
+    if (!(std::fabs(dl - 1.0) < 1e-9)) return SMCRT_ERR_BAD_SCENE;
+    if ((src->kind == SMCRT_SRC_DISC || src->kind == SMCRT_SRC_SQUARE) && !(src->radius > 0))
+        return SMCRT_ERR_BAD_SCENE;
+    for (int a = 0; a < 3; ++a) {
+        if (!finite(src->pos[a])) return SMCRT_ERR_BAD_SCENE;
+        if (g->n[a] < 1 || g->n[a] > kMaxGridSide) return SMCRT_ERR_BAD_SCENE;
+        if (!(g->lo[a] < g->hi[a]) || !finite(g->lo[a]) || !finite(g->hi[a])) return SMCRT_ERR_BAD_SCENE;
+    }
+    return SMCRT_OK;
+}
+
+// Postfix CSG -> device instruction stream.  A primitive immediately
+// followed by a binary operator becomes one fused instruction that combines
+// it with the stack top; the register stack depth must stay <= kMaxStack.
+int compile(const smcrt_scene *sc, std::vector<Instr> &ins, std::vector<double> &k64, std::vector<int2> &rr)
+{
+    for (int r = 0; r < sc->nregions; ++r) {
+        const smcrt_region &R = sc->regions[r];
+        const smcrt_csg_node *nd = sc->nodes + R.node_begin;
+        const int begin = (int)ins.size();
+        int depth = 0;
+        for (int i = 0; i < R.node_count; ++i) {
+            const int op = nd[i].op;
+            if (op == SMCRT_OP_PRIM) {
+                const int p = nd[i].prim;
+                if (p < 0 || p >= sc->nprims) return SMCRT_ERR_BAD_SCENE;
+                const int kind = sc->prims[p].kind;
+                const bool fuse = depth >= 1 && i + 1 < R.node_count && nd[i + 1].op >= SMCRT_OP_UNION &&
+                                  nd[i + 1].op <= SMCRT_OP_SUBTRACT;
+                Instr in{};
+                in.prim = p;
+                in.region = -1;
+                if (fuse) {
+                    const int bop = nd[i + 1].op;
+                    const double k = nd[i + 1].k;
+                    if (bop == SMCRT_OP_SMOOTH_UNION && !(k > 0 && finite(k))) return SMCRT_ERR_BAD_SCENE;
+                    in.op = bop | (kind << 8);
+                    const float kinv = bop == SMCRT_OP_SMOOTH_UNION ? (float)(1.0 / k) : 0.f;
+                    std::memcpy(&in.pad, &kinv, 4);
+                    ins.push_back(in);
+                    k64.push_back(bop == SMCRT_OP_SMOOTH_UNION ? k : 0.0);
+                    ++i;  // operator consumed
+                } else {
+                    in.op = 0 | (kind << 8);
+                    ins.push_back(in);
+                    k64.push_back(0.0);
+                    if (++depth > kMaxStack) return SMCRT_ERR_BAD_SCENE;
+                }
+            } else if (op >= SMCRT_OP_UNION && op <= SMCRT_OP_SUBTRACT) {
+                if (depth < 2) return SMCRT_ERR_BAD_SCENE;
+                const double k = nd[i].k;
+                if (op == SMCRT_OP_SMOOTH_UNION && !(k > 0 && finite(k))) return SMCRT_ERR_BAD_SCENE;
+                Instr in{};
+                in.op = op;
+                in.prim = -1;
+                in.region = -1;
+                const float kinv = op == SMCRT_OP_SMOOTH_UNION ? (float)(1.0 / k) : 0.f;
+                std::memcpy(&in.pad, &kinv, 4);
+                ins.push_back(in);
+                k64.push_back(op == SMCRT_OP_SMOOTH_UNION ? k : 0.0);
+                --depth;
+            } else {
+                return SMCRT_ERR_BAD_SCENE;
+            }
+        }
+        if (depth != 1) return SMCRT_ERR_BAD_SCENE;
+        ins.back().region = r;
+        rr.push_back(make_int2(begin, (int)ins.size()));
+    }
+    return SMCRT_OK;
+}
+
+struct Timer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double s() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context, plan, job
+// ---------------------------------------------------------------------------
+struct Job;
+
+struct smcrt_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    std::mutex tune_mu;
+    std::map<uint64_t, std::pair<int, int>> tuned;  // scene shape -> (blocks, threads)
+
+    // serving
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
+    uint64_t next_job_id = 1;
+    std::thread sched;
+    bool stop = false;
+    bool sched_started = false;
+    int64_t launches = 0;
+    int64_t running = 0;
+    size_t mem_in_use = 0;
+    std::vector<std::shared_ptr<Job>> to_release;   // waited jobs whose device memory can go
+};
+
+struct smcrt_plan {
+    smcrt_ctx *ctx = nullptr;
+    int precision = SMCRT_MIXED;
+    void *dbuf = nullptr;
+    DevScene *dscene = nullptr;
+    DevScene host{};
+    JobWork *djobs = nullptr;  // ring of launch descriptors
+    int ring = 64, ring_pos = 0;
+    int *dstatus = nullptr;
+    int blocks = 0, threads = 0;
+    size_t cells = 0;
+    size_t dbytes = 0;
+    uint64_t shape_key = 0;
+};
+
+namespace {
+
+int occupancy(int precision, int threads)
+{
+    return precision == SMCRT_FP64 ? occupancy_fp64(threads) : occupancy_mixed(threads);
+}
+
+cudaError_t launch_kernel(int precision, JobWork *jobs, int njobs, int *status, int blocks, int threads,
+                          cudaStream_t s)
+{
+    return precision == SMCRT_FP64 ? launch_fp64(jobs, njobs, status, blocks, threads, s)
+                                   : launch_mixed(jobs, njobs, status, blocks, threads, s);
+}
+
+uint64_t shape_key(const smcrt_scene *sc, int precision, const smcrt_grid *g)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+    mix((uint64_t)precision);
+    mix((uint64_t)sc->nprims);
+    mix((uint64_t)sc->nregions);
+    mix((uint64_t)sc->nnodes);
+    for (int i = 0; i < sc->nprims; ++i) mix((uint64_t)sc->prims[i].kind);
+    mix((uint64_t)g->n[0] * 1315423911ull + (uint64_t)g->n[1] * 2654435761ull + (uint64_t)g->n[2]);
+    return h;
+}
+
+// Validate, compile and upload a plan.  With a stream (the serving
+// scheduler) the scene buffer is allocated and filled stream-ordered, no
+// device-wide synchronisation happens, and no launch ring is created.
+int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid *g,
+               int32_t precision, smcrt_plan **out, cudaStream_t serving_stream = nullptr)
+{
+    int rc = validate(sc, src, g);
+    if (rc) return rc;
+    if (precision != SMCRT_FP64 && precision != SMCRT_MIXED) return SMCRT_ERR_BAD_ARG;
+    std::vector<Instr> ins;
+    std::vector<double> k64;
+    std::vector<int2> rr;
+    rc = compile(sc, ins, k64, rr);
+    if (rc) return rc;
+    const int np = sc->nprims, nr = sc->nregions, ni = (int)ins.size();
+
+    std::vector<int32_t> pkind(np);
+    std::vector<double> p64((size_t)np * 8, 0.0);
+    std::vector<float4> p32((size_t)np * 2, make_float4(0, 0, 0, 0));
+    for (int i = 0; i < np; ++i) {
+        const smcrt_prim &P = sc->prims[i];
+        pkind[i] = P.kind;
+        double *d = &p64[(size_t)8 * i];
+        if (P.kind == SMCRT_CAPSULE) {
+            const double bax = P.p[3] - P.p[0], bay = P.p[4] - P.p[1], baz = P.p[5] - P.p[2];
+            const double baba = bax * bax + bay * bay + baz * baz;
+            d[0] = P.p[0]; d[1] = P.p[1]; d[2] = P.p[2];
+            d[3] = bax; d[4] = bay; d[5] = baz; d[6] = P.p[6]; d[7] = baba;
+            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[6]);
+            p32[2 * i + 1] = make_float4((float)bax, (float)bay, (float)baz, (float)(1.0 / baba));
+        } else if (P.kind == SMCRT_BOX) {
+            for (int k = 0; k < 6; ++k) d[k] = P.p[k];
+            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], 0.f);
+            p32[2 * i + 1] = make_float4((float)P.p[3], (float)P.p[4], (float)P.p[5], 0.f);
+        } else {
+            for (int k = 0; k < 4; ++k) d[k] = P.p[k];
+            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[3]);
+        }
+    }
+    std::vector<double> reg64((size_t)nr * 8, 0.0);
+    std::vector<float4> reg32((size_t)nr * 2);
+    for (int r = 0; r < nr; ++r) {
+        const smcrt_region &R = sc->regions[r];
+        const double mu_t = R.mu_a + R.mu_s;
+        const double albedo = mu_t > 0.0 ? R.mu_s / mu_t : 0.0;
+        double *d = &reg64[(size_t)8 * r];
+        d[0] = R.mu_a; d[1] = R.mu_s; d[2] = R.g; d[3] = R.n; d[4] = mu_t; d[5] = albedo;
+        reg32[2 * r] = make_float4((float)mu_t, mu_t > 0 ? (float)(1.0 / mu_t) : 0.f, (float)albedo, (float)R.g);
+        reg32[2 * r + 1] = make_float4((float)R.n, (float)R.mu_a, (float)R.mu_s, 0.f);
+    }
+
+    // one device buffer: [DevScene | instr | k64 | pkind | p64 | p32 | rrange | reg64 | reg32]
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align16(off + bytes); return o; };
+    const size_t o_scene = take(sizeof(DevScene));
+    const size_t o_ins = take(sizeof(Instr) * ni);
+    const size_t o_k64 = take(sizeof(double) * ni);
+    const size_t o_kind = take(sizeof(int32_t) * np);
+    const size_t o_p64 = take(sizeof(double) * 8 * np);
+    const size_t o_p32 = take(sizeof(float4) * 2 * np);
+    const size_t o_rr = take(sizeof(int2) * nr);
+    const size_t o_r64 = take(sizeof(double) * 8 * nr);
+    const size_t o_r32 = take(sizeof(float4) * 2 * nr);
+    const size_t total = off;
+
+    std::unique_ptr<smcrt_plan> pl(new smcrt_plan());
+    pl->ctx = ctx;
+    pl->precision = precision;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return SMCRT_ERR_CUDA;
+    if (serving_stream) {
+        if (cudaMallocAsync(&pl->dbuf, total, serving_stream) != cudaSuccess) return SMCRT_ERR_NO_MEMORY;
+    } else if (cudaMalloc(&pl->dbuf, total) != cudaSuccess) {
+        return SMCRT_ERR_NO_MEMORY;
+    }
+    pl->dbytes = total;
+    char *base = (char *)pl->dbuf;
+    DevScene &H = pl->host;
+    std::memset(&H, 0, sizeof H);
+    H.instr = (const Instr *)(base + o_ins);
+    H.k64 = (const double *)(base + o_k64);
+    H.kinv32 = nullptr;
+    H.pkind = (const int32_t *)(base + o_kind);
+    H.p64 = (const double *)(base + o_p64);
+    H.p32 = (const float4 *)(base + o_p32);
+    H.rrange = (const int2 *)(base + o_rr);
+    H.reg64 = (const double *)(base + o_r64);
+    H.reg32 = (const float4 *)(base + o_r32);
+    H.ninstr = ni;
+    H.nregions = nr;
+    H.nprims = np;
+    H.precision = precision;
+    float rmax = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        H.bbc[a] = (sc->bbox_lo[a] + sc->bbox_hi[a]) * 0.5;
+        H.bbh[a] = (sc->bbox_hi[a] - sc->bbox_lo[a]) * 0.5;
+        H.bbc32[a] = (float)H.bbc[a];
+        H.bbh32[a] = (float)H.bbh[a];
+        rmax = std::max(rmax, (float)std::max(std::fabs(sc->bbox_lo[a]), std::fabs(sc->bbox_hi[a])));
+    }
+    H.delta = sc->delta;
+    H.ambient_n = sc->ambient_n;
+    H.delta32 = std::max((float)sc->delta, 64.f * ulp_f32(rmax));
+    H.h32 = 32.f * H.delta32;
+    H.max_steps = sc->max_steps;
+    H.src_kind = src->kind;
+    onb_host(src->dir, H.src_b1, H.src_b2);
+    for (int a = 0; a < 3; ++a) {
+        H.src_pos[a] = src->pos[a];
+        H.src_dir[a] = src->dir[a];
+        H.src_pos32[a] = (float)src->pos[a];
+        H.src_dir32[a] = (float)src->dir[a];
+        H.src_b132[a] = (float)H.src_b1[a];
+        H.src_b232[a] = (float)H.src_b2[a];
+        H.g_lo[a] = g->lo[a];
+        H.g_hi[a] = g->hi[a];
+        H.g_dl[a] = (g->hi[a] - g->lo[a]) / (double)g->n[a];
+        H.g_lo32[a] = (float)g->lo[a];
+        H.g_hi32[a] = (float)g->hi[a];
+        H.g_dl32[a] = (float)H.g_dl[a];
+        H.g_idl32[a] = (float)(1.0 / H.g_dl[a]);
+        H.g_n[a] = g->n[a];
+    }
+    H.src_radius = src->radius;
+    H.src_radius32 = (float)src->radius;
+
+    std::vector<char> hb(total, 0);
+    std::memcpy(hb.data() + o_scene, &H, sizeof H);
+    std::memcpy(hb.data() + o_ins, ins.data(), sizeof(Instr) * ni);
+    std::memcpy(hb.data() + o_k64, k64.data(), sizeof(double) * ni);
+    std::memcpy(hb.data() + o_kind, pkind.data(), sizeof(int32_t) * np);
+    std::memcpy(hb.data() + o_p64, p64.data(), sizeof(double) * 8 * np);
+    std::memcpy(hb.data() + o_p32, p32.data(), sizeof(float4) * 2 * np);
+    std::memcpy(hb.data() + o_rr, rr.data(), sizeof(int2) * nr);
+    std::memcpy(hb.data() + o_r64, reg64.data(), sizeof(double) * 8 * nr);
+    std::memcpy(hb.data() + o_r32, reg32.data(), sizeof(float4) * 2 * nr);
+    pl->dscene = (DevScene *)(base + o_scene);
+    pl->cells = (size_t)g->n[0] * g->n[1] * g->n[2];
+    if (serving_stream) {
+        // pageable source: staged before the call returns, so hb may go
+        if (cudaMemcpyAsync(pl->dbuf, hb.data(), total, cudaMemcpyHostToDevice, serving_stream) != cudaSuccess) {
+            cudaFreeAsync(pl->dbuf, serving_stream);
+            return SMCRT_ERR_CUDA;
+        }
+        *out = pl.release();
+        return SMCRT_OK;
+    }
+    if (cudaMemcpy(pl->dbuf, hb.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(pl->dbuf);
+        return SMCRT_ERR_CUDA;
+    }
+    if (cudaMalloc(&pl->djobs, sizeof(JobWork) * pl->ring) != cudaSuccess) {
+        cudaFree(pl->dbuf);
+        return SMCRT_ERR_NO_MEMORY;
+    }
+    if (cudaMalloc(&pl->dstatus, sizeof(int)) != cudaSuccess || cudaMemset(pl->dstatus, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(pl->dbuf);
+        cudaFree(pl->djobs);
+        return SMCRT_ERR_NO_MEMORY;
+    }
+    pl->cells = (size_t)g->n[0] * g->n[1] * g->n[2];
+    pl->shape_key = shape_key(sc, precision, g);
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tuned.find(pl->shape_key);
+        if (it != ctx->tuned.end()) {
+            pl->blocks = it->second.first;
+            pl->threads = it->second.second;
+        }
+    }
+    *out = pl.release();
+    return SMCRT_OK;
+}
+
+void default_launch(const smcrt_plan *pl, int &blocks, int &threads)
+{
+    threads = pl->threads > 0 ? pl->threads : 128;
+    blocks = pl->blocks;
+    if (blocks <= 0) {
+        const int occ = std::max(1, occupancy(pl->precision, threads));
+        blocks = pl->ctx->sm_count * occ;
+    }
+}
+
+int plan_launch_impl(smcrt_plan *pl, uint64_t id_begin, uint64_t n, uint64_t seed, int64_t *flu,
+                     smcrt_totals *tot, smcrt_packet_record *rec, cudaStream_t s, int blocks, int threads)
+{
+    JobWork jw{};
+    jw.next = id_begin;
+    jw.end = id_begin + n;
+    jw.begin = id_begin;
+    jw.seed = seed;
+    jw.fluence = (long long *)flu;
+    jw.totals = tot;
+    jw.records = rec;
+    jw.scene = pl->dscene;
+    jw.cancelled = 0;
+    JobWork *slot = pl->djobs + pl->ring_pos;
+    pl->ring_pos = (pl->ring_pos + 1) % pl->ring;
+    if (launch_set_job(slot, jw, s) != cudaSuccess) return SMCRT_ERR_CUDA;
+    if (launch_kernel(pl->precision, slot, 1, pl->dstatus, blocks, threads, s) != cudaSuccess)
+        return SMCRT_ERR_CUDA;
+    return SMCRT_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Serving: job state and scheduler
+// ---------------------------------------------------------------------------
+struct Job {
+    uint64_t id = 0;
+    // host copies of the request
+    std::vector<smcrt_prim> prims;
+    std::vector<smcrt_csg_node> nodes;
+    std::vector<smcrt_region> regions;
+    smcrt_scene scene{};
+    smcrt_source source{};
+    smcrt_grid grid{};
+    uint64_t npackets = 0, seed = 0;
+    int precision = SMCRT_MIXED;
+    // device resources while admitted
+    smcrt_plan *plan = nullptr;
+    int64_t *dflu = nullptr;
+    int slot = -1;                // index into the device totals array
+    size_t bytes = 0;
+    uint64_t cursor = 0;          // next packet id to schedule
+    double cost = 0;              // measured warp-cycles per packet (0 = unknown)
+    int64_t admit_round = 0;      // first round index that can carry this job
+    int64_t last_round = -1;      // last round index that carried its ids
+    bool admitted = false, done = false, cancelled = false, released = false;
+    int status = SMCRT_OK;
+    smcrt_totals totals{};
+    double t_submit = 0, t_done = 0;
+};
+
+namespace {
+
+constexpr int kMaxSlots = 64;
+constexpr int kRoundsInFlight = 2;
+constexpr double kRoundSeconds = 0.008;   // target device time of one round
+
+size_t job_bytes(const smcrt_grid &g)
+{
+    return (size_t)g.n[0] * g.n[1] * g.n[2] * 8 + 65536;
+}
+
+void free_job_device(Job &j, cudaStream_t st)
+{
+    if (j.plan) {
+        cudaFreeAsync(j.plan->dbuf, st);
+        delete j.plan;
+        j.plan = nullptr;
+    }
+    if (j.dflu) cudaFreeAsync(j.dflu, st);
+    j.dflu = nullptr;
+}
+
+// The scheduler thread.  Each round is one replay of a captured CUDA graph:
+//   [job tables H2D] -> fork -> {mixed kernel | FP64 kernel} -> join ->
+//   [all job totals D2H into pinned memory]
+// with up to two rounds in flight.  A round gives every admitted job a
+// quantum of packet ids sized by processor sharing: each job gets an equal
+// share of the round's warp-cycles, converted to packets with the job's
+// measured cost (busy cycles per packet from earlier rounds), so short jobs
+// finish within one round while long ones keep progressing.  Jobs join at the
+// next round after admission; completion is read from the totals snapshot.
+void scheduler(smcrt_ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    cudaStream_t st, st2;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
+    cudaEvent_t ev_fork, ev_join;
+    cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+    int *d_status = nullptr;
+    smcrt_totals *d_tot = nullptr;
+    cudaMalloc(&d_status, sizeof(int));
+    cudaMemset(d_status, 0, sizeof(int));
+    cudaMalloc(&d_tot, sizeof(smcrt_totals) * kMaxSlots);
+    cudaMemset(d_tot, 0, sizeof(smcrt_totals) * kMaxSlots);
+    int *h_status = nullptr;
+    cudaMallocHost(&h_status, sizeof(int));
+    const int threads = 128;
+    const int occ_m = std::max(1, occupancy_mixed(threads)), occ_d = std::max(1, occupancy_fp64(threads));
+    const int blocks_m = ctx->sm_count * occ_m, blocks_d = ctx->sm_count * occ_d;
+    int clk_khz = 1900000;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, ctx->device);
+    // warp-cycles one round can spend (the mixed kernel's resident warps)
+    const double round_cycles = (double)blocks_m * (threads / 32) * clk_khz * 1e3 * kRoundSeconds;
+
+    struct Buf {
+        JobWork *h_tab = nullptr, *d_tab = nullptr;   // [2 * kMaxSlots]: mixed table, then FP64 table
+        smcrt_totals *h_tot = nullptr;                // totals snapshot taken at the end of the round
+        cudaGraphExec_t graph = nullptr;
+        cudaEvent_t ev = nullptr;
+        bool busy = false;
+        int64_t idx = -1;
+    } buf[kRoundsInFlight];
+    for (auto &b : buf) {
+        cudaMallocHost(&b.h_tab, sizeof(JobWork) * 2 * kMaxSlots);
+        cudaMalloc(&b.d_tab, sizeof(JobWork) * 2 * kMaxSlots);
+        cudaMallocHost(&b.h_tot, sizeof(smcrt_totals) * kMaxSlots);
+        cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+        std::memset(b.h_tab, 0, sizeof(JobWork) * 2 * kMaxSlots);
+        cudaGraph_t g;
+        cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        cudaMemcpyAsync(b.d_tab, b.h_tab, sizeof(JobWork) * 2 * kMaxSlots, cudaMemcpyHostToDevice, st);
+        cudaEventRecord(ev_fork, st);
+        cudaStreamWaitEvent(st2, ev_fork, 0);
+        launch_mixed(b.d_tab, kMaxSlots, d_status, blocks_m, threads, st);
+        launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status, blocks_d, threads, st2);
+        cudaEventRecord(ev_join, st2);
+        cudaStreamWaitEvent(st, ev_join, 0);
+        cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
+        cudaStreamEndCapture(st, &g);
+        cudaGraphInstantiate(&b.graph, g, 0);
+        cudaGraphDestroy(g);
+    }
+
+    std::vector<std::shared_ptr<Job>> active;   // admitted, not yet complete
+    std::vector<int> free_slots;
+    for (int i = kMaxSlots - 1; i >= 0; --i) free_slots.push_back(i);
+    int cur = 0;
+    int64_t issued = 0, completed = -1;
+
+    auto is_cancelled = [&](const std::shared_ptr<Job> &j) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        return j->cancelled;
+    };
+    auto complete = [&](const std::shared_ptr<Job> &j, const smcrt_totals *t, int status) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (t) j->totals = *t;
+        j->status = status;
+        j->done = true;
+        j->t_done = now_s();
+        ctx->running -= 1;
+        free_slots.push_back(j->slot);
+        ctx->cv_done.notify_all();
+    };
+
+    for (;;) {
+        // ---- admission (FIFO, by slots and device memory) and releases
+        std::vector<std::shared_ptr<Job>> newly, released;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            const bool idle = active.empty() && !buf[0].busy && !buf[1].busy;
+            if (idle && ctx->queue.empty() && ctx->to_release.empty()) {
+                if (ctx->stop) break;
+                ctx->cv_work.wait(lk, [&] { return ctx->stop || !ctx->queue.empty() || !ctx->to_release.empty(); });
+                if (ctx->stop && ctx->queue.empty() && ctx->to_release.empty()) break;
+            }
+            released.swap(ctx->to_release);
+            while (!ctx->queue.empty() && (int)free_slots.size() > (int)newly.size()) {
+                auto j = ctx->queue.front();
+                if (ctx->mem_in_use + j->bytes > ctx->budget && !(active.empty() && newly.empty())) break;
+                ctx->queue.pop_front();
+                if (j->cancelled) {
+                    j->status = SMCRT_ERR_CANCELLED;
+                    j->done = true;
+                    j->t_done = now_s();
+                    ctx->cv_done.notify_all();
+                    continue;
+                }
+                ctx->mem_in_use += j->bytes;
+                ctx->running += 1;
+                j->admitted = true;
+                newly.push_back(j);
+            }
+        }
+        for (auto &j : released) free_job_device(*j, st);
+        for (auto &j : newly) {
+            int rc = build_plan(ctx, &j->scene, &j->source, &j->grid, j->precision, &j->plan, st);
+            const size_t fb = (size_t)j->grid.n[0] * j->grid.n[1] * j->grid.n[2] * 8;
+            if (rc == SMCRT_OK && cudaMallocAsync(&j->dflu, fb, st) != cudaSuccess) rc = SMCRT_ERR_NO_MEMORY;
+            j->slot = free_slots.back();
+            free_slots.pop_back();
+            j->admit_round = issued;     // snapshots of earlier rounds do not describe this job
+            if (rc == SMCRT_OK) {
+                cudaMemsetAsync(j->dflu, 0, fb, st);
+                cudaMemsetAsync(d_tot + j->slot, 0, sizeof(smcrt_totals), st);
+                active.push_back(j);
+            } else {
+                free_job_device(*j, st);
+                {
+                    std::lock_guard<std::mutex> lk(ctx->mu);
+                    ctx->mem_in_use -= std::min(ctx->mem_in_use, j->bytes);
+                    j->admitted = false;
+                }
+                complete(j, nullptr, rc);
+            }
+        }
+
+        // ---- reap the buffer we are about to refill
+        Buf &B = buf[cur];
+        if (B.busy) {
+            cudaEventSynchronize(B.ev);
+            B.busy = false;
+            completed = B.idx;
+            cudaMemcpy(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+            std::vector<std::shared_ptr<Job>> still;
+            for (auto &j : active) {
+                if (B.idx < j->admit_round) {
+                    still.push_back(j);
+                    continue;
+                }
+                const smcrt_totals &t = B.h_tot[j->slot];
+                if (t.packets > 0 && t.busy_cycles > 0) j->cost = (double)t.busy_cycles / (double)t.packets;
+                const bool drained = j->last_round <= completed;
+                if ((uint64_t)t.packets >= j->npackets) {
+                    complete(j, &t, *h_status ? SMCRT_ERR_DEVICE : SMCRT_OK);
+                } else if (drained && is_cancelled(j)) {
+                    complete(j, &t, SMCRT_ERR_CANCELLED);
+                } else if (drained && j->cursor >= j->npackets) {
+                    complete(j, &t, SMCRT_ERR_DEVICE);   // ids ran but packets are missing
+                } else {
+                    still.push_back(j);
+                }
+            }
+            active.swap(still);
+        }
+
+        // ---- the next round: processor-sharing quanta over runnable jobs
+        std::memset(B.h_tab, 0, sizeof(JobWork) * 2 * kMaxSlots);
+        std::vector<std::shared_ptr<Job>> runnable, keep;
+        for (auto &j : active) {
+            if (is_cancelled(j)) {
+                if (j->last_round <= completed) {   // nothing in flight: done now
+                    complete(j, nullptr, SMCRT_ERR_CANCELLED);
+                    continue;
+                }
+            } else if (j->cursor < j->npackets) {
+                runnable.push_back(j);
+            }
+            keep.push_back(j);
+        }
+        active.swap(keep);
+        if (runnable.empty()) {
+            if (buf[1 - cur].busy) cur = 1 - cur;   // reap the other round next
+            continue;
+        }
+        double known = 0;
+        int nk = 0;
+        for (auto &j : runnable)
+            if (j->cost > 0) { known += j->cost; ++nk; }
+        const double dflt = nk ? known / nk : 4.0e4;
+        const double share = round_cycles / (double)runnable.size();
+        int nm = 0, nd = 0;
+        for (auto &j : runnable) {
+            const double c = j->cost > 0 ? j->cost : dflt;
+            uint64_t q = (uint64_t)std::max(2048.0, share / c);
+            q = std::min<uint64_t>(q, j->npackets - j->cursor);
+            JobWork w{};
+            w.next = j->cursor;
+            w.end = j->cursor + q;
+            w.begin = 0;
+            w.seed = j->seed;
+            w.fluence = (long long *)j->dflu;
+            w.totals = d_tot + j->slot;
+            w.records = nullptr;
+            w.scene = j->plan->dscene;
+            w.cancelled = 0;
+            j->cursor += q;
+            j->last_round = issued;
+            if (j->precision == SMCRT_FP64) B.h_tab[kMaxSlots + nd++] = w;
+            else B.h_tab[nm++] = w;
+        }
+        cudaGraphLaunch(B.graph, st);
+        cudaEventRecord(B.ev, st);
+        B.busy = true;
+        B.idx = issued++;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->launches += 1;
+        }
+        cur = 1 - cur;
+    }
+    // shut down: wait for rounds, free everything still held
+    cudaStreamSynchronize(st);
+    for (auto &j : active) free_job_device(*j, st);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto &j : ctx->to_release) free_job_device(*j, st);
+        ctx->to_release.clear();
+        for (auto &kv : ctx->jobs) free_job_device(*kv.second, st);   // done but never waited
+    }
+    cudaStreamSynchronize(st);
+    for (auto &b : buf) {
+        cudaGraphExecDestroy(b.graph);
+        cudaEventDestroy(b.ev);
+        cudaFreeHost(b.h_tab);
+        cudaFreeHost(b.h_tot);
+        cudaFree(b.d_tab);
+    }
+    cudaFreeHost(h_status);
+    cudaEventDestroy(ev_fork);
+    cudaEventDestroy(ev_join);
+    cudaFree(d_tot);
+    cudaFree(d_status);
+    cudaStreamDestroy(st2);
+    cudaStreamDestroy(st);
+}
+
+void start_scheduler(smcrt_ctx *ctx)
+{
+    if (!ctx->sched_started) {
+        ctx->sched = std::thread(scheduler, ctx);
+        ctx->sched_started = true;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int smcrt_version(void) { return 10000; }
+
+const char *smcrt_strerror(int code)
+{
+    switch (code) {
+    case SMCRT_OK: return "ok";
+    case SMCRT_ERR_BAD_ARG: return "bad argument";
+    case SMCRT_ERR_BAD_SCENE: return "invalid scene, source or grid";
+    case SMCRT_ERR_NO_MEMORY: return "out of memory or over the device memory budget";
+    case SMCRT_ERR_CUDA: return "CUDA runtime error";
+    case SMCRT_ERR_TIMEOUT: return "timed out";
+    case SMCRT_ERR_CANCELLED: return "cancelled";
+    case SMCRT_ERR_NOT_FOUND: return "unknown job";
+    case SMCRT_ERR_DEVICE: return "kernel reported an error";
+    default: return "unknown status";
+    }
+}
+
+int smcrt_validate(const smcrt_scene *scene, const smcrt_source *source, const smcrt_grid *grid, int32_t *ninstr)
+{
+    int rc = validate(scene, source, grid);
+    if (rc) return rc;
+    std::vector<Instr> ins;
+    std::vector<double> k64;
+    std::vector<int2> rr;
+    rc = compile(scene, ins, k64, rr);
+    if (rc) return rc;
+    if (ninstr) *ninstr = (int32_t)ins.size();
+    return SMCRT_OK;
+}
+
+int smcrt_create(smcrt_ctx **out, int device, size_t budget)
+{
+    if (!out) return SMCRT_ERR_BAD_ARG;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SMCRT_ERR_BAD_ARG;
+    CU(cudaSetDevice(device));
+    std::unique_ptr<smcrt_ctx> c(new smcrt_ctx());
+    c->device = device;
+    CU(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    size_t fr = 0, tot = 0;
+    CU(cudaMemGetInfo(&fr, &tot));
+    c->budget = budget ? budget : (size_t)(0.8 * (double)fr);
+    *out = c.release();
+    return SMCRT_OK;
+}
+
+int smcrt_destroy(smcrt_ctx *ctx)
+{
+    if (!ctx) return SMCRT_ERR_BAD_ARG;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv_work.notify_all();
+    if (ctx->sched_started) ctx->sched.join();
+    delete ctx;
+    return SMCRT_OK;
+}
+
+int smcrt_plan_create(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *source,
+                      const smcrt_grid *grid, int32_t precision, smcrt_plan **out)
+{
+    if (!ctx || !out) return SMCRT_ERR_BAD_ARG;
+    return build_plan(ctx, scene, source, grid, precision, out);
+}
+
+int smcrt_plan_destroy(smcrt_plan *pl)
+{
+    if (!pl) return SMCRT_ERR_BAD_ARG;
+    cudaSetDevice(pl->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(pl->dbuf);
+    cudaFree(pl->djobs);
+    cudaFree(pl->dstatus);
+    delete pl;
+    return SMCRT_OK;
+}
+
+int smcrt_plan_set_launch(smcrt_plan *pl, int32_t blocks, int32_t threads)
+{
+    if (!pl || blocks < 0 || threads < 0 || threads > kMaxThreads || (threads % 32) != 0) return SMCRT_ERR_BAD_ARG;
+    pl->blocks = blocks;
+    pl->threads = threads;
+    return SMCRT_OK;
+}
+
+int smcrt_plan_launch(smcrt_plan *pl, uint64_t id_begin, uint64_t npackets, uint64_t seed, int64_t *fluence_dev,
+                      smcrt_totals *totals_dev, smcrt_packet_record *records_dev, void *stream)
+{
+    if (!pl || !totals_dev) return SMCRT_ERR_BAD_ARG;
+    if (npackets == 0) return SMCRT_OK;
+    if (id_begin + npackets < id_begin) return SMCRT_ERR_BAD_ARG;
+    int blocks, threads;
+    default_launch(pl, blocks, threads);
+    return plan_launch_impl(pl, id_begin, npackets, seed, fluence_dev, totals_dev, records_dev,
+                            (cudaStream_t)stream, blocks, threads);
+}
+
+int smcrt_plan_status(smcrt_plan *pl, int32_t *status)
+{
+    if (!pl || !status) return SMCRT_ERR_BAD_ARG;
+    int v = 0;
+    CU(cudaMemcpy(&v, pl->dstatus, sizeof v, cudaMemcpyDeviceToHost));
+    CU(cudaMemset(pl->dstatus, 0, sizeof(int)));
+    *status = v;
+    return SMCRT_OK;
+}
+
+int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int32_t *threads_out)
+{
+    if (!pl || trial == 0) return SMCRT_ERR_BAD_ARG;
+    CU(cudaSetDevice(pl->ctx->device));
+    int64_t *flu = nullptr;
+    smcrt_totals *tot = nullptr;
+    if (cudaMalloc(&flu, pl->cells * 8) != cudaSuccess) return SMCRT_ERR_NO_MEMORY;
+    if (cudaMalloc(&tot, sizeof(smcrt_totals)) != cudaSuccess) {
+        cudaFree(flu);
+        return SMCRT_ERR_NO_MEMORY;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bb = 0, bt = 0;
+    const int thread_opts[] = {64, 96, 128};
+    for (int t : thread_opts) {
+        const int occ = occupancy(pl->precision, t);
+        if (occ < 1) continue;
+        for (int mult : {1, 2, 4}) {
+            const int b = pl->ctx->sm_count * occ * mult;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaMemsetAsync(flu, 0, pl->cells * 8, 0);
+                cudaMemsetAsync(tot, 0, sizeof(smcrt_totals), 0);
+                cudaEventRecord(e0, 0);
+                int rc = plan_launch_impl(pl, 0, trial, 12345, flu, tot, nullptr, 0, b, t);
+                cudaEventRecord(e1, 0);
+                if (rc != SMCRT_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaFree(flu);
+                    cudaFree(tot);
+                    return SMCRT_ERR_CUDA;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_best = std::min(ms_best, ms);
+            }
+            if (ms_best < best) {
+                best = ms_best;
+                bb = b;
+                bt = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(flu);
+    cudaFree(tot);
+    pl->blocks = bb;
+    pl->threads = bt;
+    {
+        std::lock_guard<std::mutex> lk(pl->ctx->tune_mu);
+        pl->ctx->tuned[pl->shape_key] = {bb, bt};
+    }
+    if (blocks_out) *blocks_out = bb;
+    if (threads_out) *threads_out = bt;
+    return SMCRT_OK;
+}
+
+int smcrt_run(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *source, const smcrt_grid *grid,
+              uint64_t npackets, uint64_t seed, int32_t precision, int64_t *fluence_out, smcrt_totals *totals_out)
+{
+    if (!ctx || !totals_out) return SMCRT_ERR_BAD_ARG;
+    smcrt_plan *pl = nullptr;
+    int rc = build_plan(ctx, scene, source, grid, precision, &pl);
+    if (rc) return rc;
+    const size_t fb = pl->cells * 8;
+    int64_t *dflu = nullptr;
+    smcrt_totals *dtot = nullptr;
+    const bool dev_out = fluence_out && is_device_ptr(fluence_out);
+    rc = SMCRT_OK;
+    if (fluence_out) {
+        if (dev_out) dflu = fluence_out;
+        else if (cudaMalloc(&dflu, fb) != cudaSuccess) rc = SMCRT_ERR_NO_MEMORY;
+    }
+    if (rc == SMCRT_OK && cudaMalloc(&dtot, sizeof(smcrt_totals)) != cudaSuccess) rc = SMCRT_ERR_NO_MEMORY;
+    if (rc == SMCRT_OK) {
+        if (dflu && cudaMemsetAsync(dflu, 0, fb, 0) != cudaSuccess) rc = SMCRT_ERR_CUDA;
+        if (cudaMemsetAsync(dtot, 0, sizeof(smcrt_totals), 0) != cudaSuccess) rc = SMCRT_ERR_CUDA;
+    }
+    if (rc == SMCRT_OK && npackets > 0) {
+        int blocks, threads;
+        default_launch(pl, blocks, threads);
+        rc = plan_launch_impl(pl, 0, npackets, seed, dflu, dtot, nullptr, 0, blocks, threads);
+    }
+    smcrt_totals t{};
+    if (rc == SMCRT_OK) {
+        if (cudaMemcpy(&t, dtot, sizeof t, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SMCRT_ERR_CUDA;
+        else if (fluence_out && !dev_out && cudaMemcpy(fluence_out, dflu, fb, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = SMCRT_ERR_CUDA;
+    }
+    int32_t ks = 0;
+    if (rc == SMCRT_OK && smcrt_plan_status(pl, &ks) == SMCRT_OK && ks) rc = SMCRT_ERR_DEVICE;
+    if (rc == SMCRT_OK) *totals_out = t;
+    if (dflu && !dev_out) cudaFree(dflu);
+    if (dtot) cudaFree(dtot);
+    smcrt_plan_destroy(pl);
+    return rc;
+}
+
+int smcrt_submit(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *source, const smcrt_grid *grid,
+                 uint64_t npackets, uint64_t seed, int32_t precision, uint64_t *job_id)
+{
+    if (!ctx || !job_id) return SMCRT_ERR_BAD_ARG;
+    if (precision != SMCRT_FP64 && precision != SMCRT_MIXED) return SMCRT_ERR_BAD_ARG;
+    int rc = validate(scene, source, grid);
+    if (rc) return rc;
+    std::vector<Instr> ins;
+    std::vector<double> k64;
+    std::vector<int2> rr;
+    rc = compile(scene, ins, k64, rr);
+    if (rc) return rc;
+    auto j = std::make_shared<Job>();
+    j->prims.assign(scene->prims, scene->prims + scene->nprims);
+    j->nodes.assign(scene->nodes, scene->nodes + scene->nnodes);
+    j->regions.assign(scene->regions, scene->regions + scene->nregions);
+    j->scene = *scene;
+    j->scene.prims = j->prims.data();
+    j->scene.nodes = j->nodes.data();
+    j->scene.regions = j->regions.data();
+    j->source = *source;
+    j->grid = *grid;
+    j->npackets = npackets;
+    j->seed = seed;
+    j->precision = precision;
+    j->t_submit = now_s();
+    j->bytes = job_bytes(*grid);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (j->bytes > ctx->budget) return SMCRT_ERR_NO_MEMORY;
+        j->id = ctx->next_job_id++;
+        ctx->jobs[j->id] = j;
+        if (npackets == 0) {
+            j->done = true;
+            j->t_done = j->t_submit;
+        } else {
+            ctx->queue.push_back(j);
+        }
+        *job_id = j->id;
+        start_scheduler(ctx);
+    }
+    ctx->cv_work.notify_all();
+    return SMCRT_OK;
+}
+
+int smcrt_poll(smcrt_ctx *ctx, uint64_t job_id, int32_t *done)
+{
+    if (!ctx || !done) return SMCRT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(job_id);
+    if (it == ctx->jobs.end()) return SMCRT_ERR_NOT_FOUND;
+    *done = it->second->done ? 1 : 0;
+    return SMCRT_OK;
+}
+
+int smcrt_wait(smcrt_ctx *ctx, uint64_t job_id, double timeout_s, int64_t *fluence_out, smcrt_totals *totals_out,
+               double *latency_s)
+{
+    if (!ctx) return SMCRT_ERR_BAD_ARG;
+    std::shared_ptr<Job> j;
+    {
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        auto it = ctx->jobs.find(job_id);
+        if (it == ctx->jobs.end()) return SMCRT_ERR_NOT_FOUND;
+        j = it->second;
+        auto pred = [&] { return j->done; };
+        if (timeout_s < 0) {
+            ctx->cv_done.wait(lk, pred);
+        } else if (!ctx->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
+            return SMCRT_ERR_TIMEOUT;
+        }
+        ctx->jobs.erase(job_id);
+    }
+    int rc = j->status;
+    cudaSetDevice(ctx->device);
+    if (rc == SMCRT_OK) {
+        if (fluence_out && j->dflu) {
+            const size_t fb = (size_t)j->grid.n[0] * j->grid.n[1] * j->grid.n[2] * 8;
+            if (cudaMemcpy(fluence_out, j->dflu, fb, cudaMemcpyDefault) != cudaSuccess) rc = SMCRT_ERR_CUDA;
+        } else if (fluence_out && j->npackets == 0) {
+            std::memset(fluence_out, 0, (size_t)j->grid.n[0] * j->grid.n[1] * j->grid.n[2] * 8);
+        }
+        if (totals_out) *totals_out = j->totals;
+    }
+    if (latency_s) *latency_s = j->t_done - j->t_submit;
+    if (j->admitted) {   // the scheduler frees the device memory, stream-ordered
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->mem_in_use -= std::min(ctx->mem_in_use, j->bytes);
+            j->admitted = false;
+            ctx->to_release.push_back(j);
+        }
+        ctx->cv_work.notify_all();
+    }
+    return rc;
+}
+
+int smcrt_cancel(smcrt_ctx *ctx, uint64_t job_id)
+{
+    if (!ctx) return SMCRT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(job_id);
+    if (it == ctx->jobs.end()) return SMCRT_ERR_NOT_FOUND;
+    it->second->cancelled = true;
+    return SMCRT_OK;
+}
+
+int smcrt_serving_stats(smcrt_ctx *ctx, int64_t *queued, int64_t *running, int64_t *launches)
+{
+    if (!ctx) return SMCRT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (queued) *queued = (int64_t)ctx->queue.size();
+    if (running) *running = ctx->running;
+    if (launches) *launches = ctx->launches;
+    return SMCRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// smcrt_internal.h -- structures shared by the host runtime (smcrt_api.cpp)
+// and the two packet-kernel translation units (FP64 and mixed precision).
+// Not part of the public C-ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/smcrt.h"
+
+namespace smcrt {
+
+constexpr int kMaxStack = 4;      // CSG register stack depth on the device
+constexpr int kMaxRegions = 64;
+constexpr int kMaxPrims = 4096;
+constexpr int kMaxGridSide = 1024;
+constexpr int kMaxThreads = 128;   // packet kernels are compiled for <= 128 threads per block
+
+// Device instruction (compiled CSG program).  op: 0 push primitive;
+// 1 union, 2 smooth union, 3 intersect, 4 subtract.  prim >= 0 with a
+// binary op means "combine the stack top (left) with this primitive
+// (right)"; prim < 0 with a binary op combines the top two stack entries.
+// region >= 0 marks the last instruction of that region's program.
+struct Instr {
+    int32_t op;
+    int32_t prim;
+    int32_t region;
+    int32_t pad;
+};
+
+// Scene + source + grid of one plan as the kernels read them.  Lives in
+// device memory; each warp stages a copy in shared memory when it starts
+// on a job.  All double fields are computed on the host with the same
+// expressions the FP64 reference uses, so the FP64 kernel sees identical
+// values.
+struct DevScene {
+    // instruction stream and primitive tables (device pointers)
+    const Instr *instr;
+    const double *k64;        // smooth radius per instruction
+    const float *kinv32;      // 1/k per instruction (FP32 path)
+    const int32_t *pkind;     // per primitive: 0 sphere, 1 box, 2 capsule
+    const double *p64;        // 8 per primitive (capsule: a, b-a, r, |b-a|^2)
+    const float4 *p32;        // 2 per primitive (capsule: a|r, b-a|1/|b-a|^2)
+    const int2 *rrange;       // per region: instruction [begin, end)
+    const double *reg64;      // 8 per region: mu_a, mu_s, g, n, mu_t, albedo, 0, 0
+    const float4 *reg32;      // per region: mu_t, albedo, g, n
+    int32_t ninstr, nregions, nprims, precision;
+    // bounding box as centre / half extent
+    double bbc[3], bbh[3];
+    float bbc32[3], bbh32[3];
+    double delta, ambient_n;
+    float delta32;            // FP32 surface threshold (>= 64 ulp of the scene extent)
+    float h32;                // FP32 central-difference step for normals
+    int64_t max_steps;
+    // source
+    int32_t src_kind, pad0;
+    double src_pos[3], src_dir[3], src_b1[3], src_b2[3], src_radius;
+    float src_pos32[3], src_dir32[3], src_b132[3], src_b232[3], src_radius32;
+    // grid (fluence voxels; n = 0 disables the tally)
+    double g_lo[3], g_hi[3], g_dl[3];
+    float g_lo32[3], g_hi32[3], g_dl32[3], g_idl32[3];
+    int32_t g_n[3], pad1;
+};
+
+// Work descriptor of one job in a launch.  `next` is the packet-id cursor
+// the warps claim from with atomicAdd.
+struct JobWork {
+    unsigned long long next;      // next packet id to hand out
+    unsigned long long end;       // one past the last id
+    unsigned long long begin;     // first id (records are indexed id - begin)
+    unsigned long long seed;
+    long long *fluence;           // device, may be null
+    smcrt_totals *totals;         // device
+    smcrt_packet_record *records; // device, may be null
+    const DevScene *scene;        // device
+    int32_t cancelled;            // host-set: stop handing out ids
+    int32_t pad;
+};
+
+// Kernel status word bits.
+constexpr int kStatusBadJob = 1;
+constexpr int kStatusStackOverflow = 2;
+
+// Launch wrappers, one per translation unit.
+cudaError_t launch_fp64(JobWork *jobs, int njobs, int *status, int blocks, int threads,
+                        cudaStream_t stream);
+cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int threads,
+                         cudaStream_t stream);
+int occupancy_fp64(int threads);
+int occupancy_mixed(int threads);
+cudaError_t launch_set_job(JobWork *dst, const JobWork &v, cudaStream_t stream);
+
+}  // namespace smcrt

@@ -1,0 +1,462 @@
+// smcrt_k32.cu -- mixed-precision packet kernel.
+//
+// Sphere tracing, HG scattering, roulette and the DDA tally run in FP32
+// (compiled with approximate FP32 division/sqrt).  The surface threshold
+// delta32 is at least 64 FP32 ulps of the scene extent, the normal is a
+// central difference with step h32 = 32 delta32.  FP64 is used only where
+// the Fresnel/Snell cosines are ill-conditioned: near grazing (cos_i < 0.05)
+// and within 0.01 of the critical angle's sin^2 = 1, where the point is re-localised and
+// the normal and cosines recomputed in FP64 (Sec. 2.3 interface handling).
+// Tallies are the same exact int64 fixed point as the FP64 path.
+#include "smcrt_kernel.cuh"
+
+namespace smcrt {
+
+namespace {
+
+constexpr float kGrazeCos = 0.05f;    // FP64 refinement below this |cos_i|
+constexpr float kCritBand = 0.01f;    // ... and within this band of sin^2_t = 1
+
+__device__ __forceinline__ float hg_cos32(float g, float xi)
+{
+    float c;
+    if (fabsf(g) < 1e-6f) {
+        c = 2.f * xi - 1.f;
+    } else {
+        const float t = __fdividef(1.f - g * g, 1.f - g + 2.f * g * xi);
+        c = __fdividef(1.f + g * g - t * t, 2.f * g);
+    }
+    return fminf(fmaxf(c, -1.f), 1.f);
+}
+
+__device__ __forceinline__ void normalise32(float &x, float &y, float &z)
+{
+    const float il = rsqrtf(x * x + y * y + z * z);
+    x *= il; y *= il; z *= il;
+}
+
+__device__ __forceinline__ void scatter32(float &ux, float &uy, float &uz, float ct, float xi_phi)
+{
+    const float st = sqrtf(fmaxf((1.f - ct) * (1.f + ct), 0.f));
+    float sp, cp;
+    __sincosf(6.2831853f * xi_phi, &sp, &cp);
+    float b1[3], b2[3];
+    onb32(ux, uy, uz, b1, b2);
+    const float a1 = st * cp, a2 = st * sp;
+    float vx = a1 * b1[0] + a2 * b2[0] + ct * ux;
+    float vy = a1 * b1[1] + a2 * b2[1] + ct * uy;
+    float vz = a1 * b1[2] + a2 * b2[2] + ct * uz;
+    normalise32(vx, vy, vz);
+    ux = vx; uy = vy; uz = vz;
+}
+
+__device__ __forceinline__ float region_n32(const DevScene &S, int r)
+{
+    return r < 0 ? (float)S.ambient_n : __ldg(S.reg32 + 2 * r + 1).x;
+}
+
+__device__ __forceinline__ double region_n64(const DevScene &S, int r)
+{
+    return r < 0 ? S.ambient_n : __ldg(S.reg64 + 8 * r + 3);
+}
+
+// FP64 interface localisation for a crossing whose normal must be accurate:
+// four FP64 evaluations of the surface's own SDF program -- d(p), then
+// forward differences d(p + delta e_a) for the normal (truncation error
+// delta * curvature) -- a Newton step onto the surface along that normal,
+// and the Fresnel decision (uniform xi), reflected or refracted direction
+// and push-off, all in FP64.
+__device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, int rfar, float sg32, uint32_t xiw,
+                                      float &px, float &py, float &pz, float &ux, float &uy, float &uz,
+                                      float nx32, float ny32, float nz32)
+{
+    const double x = px, y = py, z = pz;
+    const double h = S.delta;
+    const double d0 = surface64(S, istar, x, y, z);
+    const double gx = surface64(S, istar, x + h, y, z) - d0;
+    const double gy = surface64(S, istar, x, y + h, z) - d0;
+    const double gz = surface64(S, istar, x, y, z + h) - d0;
+    double nx = nx32, ny = ny32, nz = nz32;
+    const double l2 = gx * gx + gy * gy + gz * gz;
+    if (l2 > 0.0) {
+        const double il = 1.0 / sqrt(l2);
+        nx = gx * il; ny = gy * il; nz = gz * il;
+    }
+    const double qx = x - d0 * nx, qy = y - d0 * ny, qz = z - d0 * nz;
+    double vx = ux, vy = uy, vz = uz;
+    const double c = vx * nx + vy * ny + vz * nz;
+    const double sg = c > 0.0 ? 1.0 : -1.0;
+    const double e = 2.0 * (double)S.delta32 * sg;
+    if (sg != (double)sg32) {   // tangent in FP64: no crossing, stay on the near side
+        const double en = -2.0 * (double)S.delta32 * (double)sg32;
+        px = (float)(qx + en * nx);
+        py = (float)(qy + en * ny);
+        pz = (float)(qz + en * nz);
+        return;
+    }
+    const double n1 = region_n64(S, rnear), n2 = region_n64(S, rfar);
+    const double ci = fabs(c);
+    const double eta = n1 / n2;
+    const double st2 = eta * eta * ((1.0 - ci) * (1.0 + ci));
+    double R = 1.0, ct = 0.0;
+    if (st2 < 1.0) {
+        ct = sqrt(1.0 - st2);
+        const double rs = (n1 * ci - n2 * ct) / (n1 * ci + n2 * ct);
+        const double rp = (n1 * ct - n2 * ci) / (n1 * ct + n2 * ci);
+        R = 0.5 * (rs * rs + rp * rp);
+    }
+    double sx;
+    if (u01_64(xiw) <= R) {
+        const double c2 = 2.0 * c;
+        vx -= c2 * nx; vy -= c2 * ny; vz -= c2 * nz;
+        sx = -e;
+    } else {
+        const double k = sg * (eta * ci - ct);
+        vx = eta * vx - k * nx; vy = eta * vy - k * ny; vz = eta * vz - k * nz;
+        sx = e;
+    }
+    const double il = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
+    ux = (float)(vx * il); uy = (float)(vy * il); uz = (float)(vz * il);
+    px = (float)(qx + sx * nx); py = (float)(qy + sx * ny); pz = (float)(qz + sx * nz);
+}
+
+// Per-warp shared state: the staged scene and the warp's tally slots.
+struct WarpShared {
+    DevScene S;
+    WarpAcc acc;
+};
+
+// One warp works through packet ids of job J until the job's cursor passes
+// its end.  Iteration structure (all lanes execute every stage; a lane's
+// phase only selects operands or predicates a short update):
+//   1 refill dead lanes (one atomicAdd per warp),
+//   2 one FP32 scene evaluation at the lane's phase point,
+//   3 classify: escape / start interface / move / normal bookkeeping /
+//     far-near regions / Fresnel,
+//   4 the track-length tally of this iteration's move (one call site),
+//   5 one Philox call serving launch, interaction and Fresnel draws,
+//   6 the consumers: release a packet, scatter (HG + roulette), Fresnel.
+__device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int lane)
+{
+    long long *const flu = J->fluence;
+    smcrt_packet_record *const recs = J->records;
+    const unsigned long long end = J->end, begin = J->begin;
+    const uint32_t k0 = (uint32_t)J->seed, k1 = (uint32_t)(J->seed >> 32);
+    const float delta = S.delta32, hstep = S.h32;
+
+    bool alive = false, retired = false;
+    float px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0, w = 0, tau = 0;
+    float qx = 0, qy = 0, qz = 0;        // NRM: gradient; FAR / NEAR: surface point
+    float nx = 0, ny = 0, nz = 0, cdot = 0, fplus = 0, dstar = 0;
+    int phase = kTrace, sub = 0, istar = -1, reg = -1, rfar = -1;
+    int nsteps = 0;
+    unsigned pscat = 0, npieces = 0;
+    long long pA = 0, pG = 0, evals = 0;
+    uint32_t id_lo = 0, id_hi = 0, event = 0;
+
+    auto finish = [&](long long dR, long long dT, long long dK) {
+        wadd(wa, kR, dR); wadd(wa, kT, dT); wadd(wa, kKilled, dK);
+        wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
+        wadd(wa, kPackets, 1);
+        if (recs) {
+            smcrt_packet_record r;
+            r.R = dR; r.T = dT; r.A = pA; r.killed = dK; r.gain = pG;
+            r.scatters = pscat; r.steps = nsteps; r.reserved = 0;
+            const unsigned long long id = ((unsigned long long)id_hi << 32) | id_lo;
+            recs[id - begin] = r;
+        }
+        alive = false;
+    };
+    auto escape = [&]() {
+        const long long v = fx32(w);
+        if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) finish(v, 0, 0);
+        else finish(0, v, 0);
+    };
+
+    for (;;) {
+        // ---- 1. refill
+        {
+            const bool want = !alive && !retired;
+            const unsigned need = __ballot_sync(SMCRT_FULL, want);
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                unsigned long long base = 0;
+                if (lane == leader)
+                    base = (*(volatile int32_t *)&J->cancelled)
+                               ? ~0ull
+                               : atomicAdd(&J->next, (unsigned long long)__popc(need));
+                base = __shfl_sync(SMCRT_FULL, base, leader);
+                if (want) {
+                    const unsigned long long id = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+                    if (base == ~0ull || id >= end) {
+                        retired = true;
+                    } else {
+                        id_lo = (uint32_t)id;
+                        id_hi = (uint32_t)(id >> 32);
+                        event = 0u;
+                        phase = kLaunch;
+                        alive = true;
+                    }
+                }
+            }
+            if (__all_sync(SMCRT_FULL, retired)) break;
+        }
+
+        // ---- 2. the scene evaluation of this iteration
+        const float sg = cdot > 0.f ? 1.f : -1.f;
+        float ex = px, ey = py, ez = pz;
+        int sel = -2;
+        if (phase == kNrm) {
+            const float hh = (sub & 1) ? -hstep : hstep;
+            const int a = sub >> 1;
+            if (a == 0) ex = px + hh; else if (a == 1) ey = py + hh; else ez = pz + hh;
+            sel = istar;
+        } else if (phase == kFar || phase == kNear) {
+            const float e = (phase == kFar ? 2.f : -2.f) * delta * sg;
+            ex = qx + e * nx; ey = qy + e * ny; ez = qz + e * nz;
+        }
+        const Eval32 E = scene_eval32(S, ex, ey, ez, sel);
+        evals += __popc(__ballot_sync(SMCRT_FULL, alive && phase != kLaunch));
+
+        // ---- 3. classify
+        bool move = false, fresnel = false, iter_done = false;
+        float L = 0.f;
+        int rnear = -1;
+        if (alive) {
+            if (phase == kTrace) {
+                if (E.dbox > 0.f) {
+                    escape();
+                } else {
+                    reg = E.region;
+                    if (E.dmin < delta) {
+                        istar = E.istar;
+                        dstar = E.dstar;
+                        phase = kNrm;
+                        sub = 0;
+                    } else {
+                        L = E.dmin - 0.5f * delta;
+                        move = true;
+                    }
+                }
+            } else if (phase == kNrm) {
+                const float f = E.dsel;
+                if ((sub & 1) == 0) {
+                    fplus = f;
+                } else {
+                    const float gg = fplus - f;
+                    const int a = sub >> 1;
+                    if (a == 0) qx = gg; else if (a == 1) qy = gg; else qz = gg;
+                }
+                if (++sub == 6) {
+                    const float l2 = qx * qx + qy * qy + qz * qz;
+                    bool approaching = false;
+                    if (l2 > 0.f) {
+                        const float il = rsqrtf(l2);
+                        nx = qx * il; ny = qy * il; nz = qz * il;
+                        cdot = ux * nx + uy * ny + uz * nz;
+                        approaching = (cdot > 0.f && dstar < 0.f) || (cdot < 0.f && dstar >= 0.f);
+                    }
+                    if (!approaching) {
+                        L = delta;                  // forced step along u
+                        move = true;
+                    } else if (istar < 0) {
+                        escape();
+                    } else {
+                        wadd(wa, kIntf, 1);
+                        qx = px - dstar * nx; qy = py - dstar * ny; qz = pz - dstar * nz;
+                        phase = kFar;
+                    }
+                }
+            } else if (phase == kFar) {
+                rfar = E.region;
+                phase = kNear;
+            } else if (phase == kNear) {
+                rnear = E.region;
+                if (region_n32(S, rnear) == region_n32(S, rfar)) {
+                    const float e = 2.f * delta * sg;
+                    px = qx + e * nx; py = qy + e * ny; pz = qz + e * nz;
+                    phase = kTrace;
+                    iter_done = true;
+                } else {
+                    fresnel = true;
+                }
+            }
+        }
+
+        // ---- 4. move: interaction point or sphere-trace step, one tally site
+        bool interact = false;
+        if (move) {
+            float mu_t = 0.f, imu_t = 0.f;
+            if (reg >= 0) {
+                const float4 RG = __ldg(S.reg32 + 2 * reg);
+                mu_t = RG.x; imu_t = RG.y;
+            }
+            interact = mu_t > 0.f && tau < mu_t * L;
+            const float seg = interact ? tau * imu_t : L;
+            if (flu) tally32(S, flu, px, py, pz, ux, uy, uz, seg, w, &npieces);
+            px += seg * ux; py += seg * uy; pz += seg * uz;
+            tau -= mu_t * seg;
+            phase = kTrace;
+            iter_done = true;
+        }
+
+        // ---- 5. one Philox call for every lane that draws this iteration
+        const bool draws = alive && (phase == kLaunch || interact || fresnel);
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        if (__any_sync(SMCRT_FULL, draws)) {
+            r = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), k0, k1);
+            if (draws) event += 1u;
+        }
+
+        // ---- 6. consumers
+        if (alive && phase == kLaunch) {           // photon release (Sec. 2.1)
+            const float x0 = u01_32(r.x), x1 = u01_32(r.y);
+            px = S.src_pos32[0]; py = S.src_pos32[1]; pz = S.src_pos32[2];
+            ux = S.src_dir32[0]; uy = S.src_dir32[1]; uz = S.src_dir32[2];
+            if (S.src_kind == 1 || S.src_kind == 2) {
+                float c1, c2;
+                if (S.src_kind == 1) {
+                    const float rho = S.src_radius32 * sqrtf(x0);
+                    float sn, cs;
+                    __sincosf(6.2831853f * x1, &sn, &cs);
+                    c1 = rho * cs;
+                    c2 = rho * sn;
+                } else {
+                    c1 = S.src_radius32 * (2.f * x0 - 1.f);
+                    c2 = S.src_radius32 * (2.f * x1 - 1.f);
+                }
+                px += c1 * S.src_b132[0] + c2 * S.src_b232[0];
+                py += c1 * S.src_b132[1] + c2 * S.src_b232[1];
+                pz += c1 * S.src_b132[2] + c2 * S.src_b232[2];
+            } else if (S.src_kind == 3) {
+                const float ct = 2.f * x0 - 1.f;
+                const float st = sqrtf(fmaxf((1.f - ct) * (1.f + ct), 0.f));
+                float sn, cs;
+                __sincosf(6.2831853f * x1, &sn, &cs);
+                ux = st * cs; uy = st * sn; uz = ct;
+            }
+            tau = -__logf(u01_32(r.w));
+            w = 1.f;
+            nsteps = 0; pA = 0; pG = 0; pscat = 0;
+            phase = kTrace;
+        }
+        if (interact) {                            // implicit capture, HG, roulette
+            const float4 RG = __ldg(S.reg32 + 2 * reg);
+            const float wn = w * RG.z;
+            pA += fx32(w - wn);
+            w = wn;
+            scatter32(ux, uy, uz, hg_cos32(RG.w, u01_32(r.x)), u01_32(r.y));
+            pscat += 1u;
+            tau = -__logf(u01_32(r.w));
+            if (w < (float)kWRoulette) {
+                if (u01_32(r.z) <= (float)(1.0 / kRouletteM)) {
+                    pG += fx32(w * (float)(kRouletteM - 1.0));
+                    w = w * (float)kRouletteM;
+                } else {
+                    finish(0, 0, fx32(w));
+                }
+            }
+        }
+        if (fresnel) {                             // reflect or refract (Sec. 2.3)
+            wadd(wa, kFres, 1);
+            const float n1 = region_n32(S, rnear), n2 = region_n32(S, rfar);
+            const float ci = fabsf(cdot);
+            const float eta = n1 / n2;
+            const float st2 = eta * eta * ((1.f - ci) * (1.f + ci));
+            const int zeros = (nx == 0.f) + (ny == 0.f) + (nz == 0.f);
+            if (ci < kGrazeCos || fabsf(st2 - 1.f) < kCritBand || zeros != 2) {
+                wadd(wa, kRefined, 1);
+                refine64(S, istar, rnear, rfar, sg, r.x, qx, qy, qz, ux, uy, uz, nx, ny, nz);
+                px = qx; py = qy; pz = qz;
+            } else {                               // planar face: the FP32 normal is exact
+                float R = 1.f, ct = 0.f;
+                if (st2 < 1.f) {
+                    ct = sqrtf(1.f - st2);
+                    const float rs = __fdividef(n1 * ci - n2 * ct, n1 * ci + n2 * ct);
+                    const float rp = __fdividef(n1 * ct - n2 * ci, n1 * ct + n2 * ci);
+                    R = 0.5f * (rs * rs + rp * rp);
+                }
+                const float e = 2.f * delta * sg;
+                if (u01_32(r.x) <= R) {
+                    const float c2 = 2.f * cdot;
+                    ux -= c2 * nx; uy -= c2 * ny; uz -= c2 * nz;
+                    normalise32(ux, uy, uz);
+                    px = qx - e * nx; py = qy - e * ny; pz = qz - e * nz;
+                } else {
+                    const float k = sg * (eta * ci - ct);
+                    ux = eta * ux - k * nx; uy = eta * uy - k * ny; uz = eta * uz - k * nz;
+                    normalise32(ux, uy, uz);
+                    px = qx + e * nx; py = qy + e * ny; pz = qz + e * nz;
+                }
+            }
+            phase = kTrace;
+            iter_done = true;
+        }
+        if (iter_done && alive) {
+            nsteps += 1;
+            if (nsteps >= S.max_steps) {
+                wadd(wa, kCap, 1);
+                finish(0, 0, fx32(w));
+            }
+        }
+    }
+    const long long pc = warp_sum((long long)npieces);
+    if (lane == 0) {
+        wadd(wa, kPieces, pc);
+        wadd(wa, kEvals, evals);
+    }
+}
+
+__global__ void __launch_bounds__(128, 5) packets_mixed(JobWork *jobs, int njobs, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    WarpShared *ws = reinterpret_cast<WarpShared *>(smem) + warp;
+    for (int jj = 0; jj < njobs; ++jj) {
+        JobWork *J = jobs + (gw + jj) % njobs;
+        unsigned long long nxt = 0, e = 0;
+        const DevScene *src = nullptr;
+        if (lane == 0) {
+            nxt = *(volatile unsigned long long *)&J->next;
+            e = J->end;
+            src = J->scene;
+        }
+        nxt = __shfl_sync(SMCRT_FULL, nxt, 0);
+        e = __shfl_sync(SMCRT_FULL, e, 0);
+        src = (const DevScene *)__shfl_sync(SMCRT_FULL, (unsigned long long)src, 0);
+        if (nxt >= e) continue;
+        if (src == nullptr || J->totals == nullptr) {
+            if (lane == 0) atomicOr(status, kStatusBadJob);
+            continue;
+        }
+        const long long *s8 = reinterpret_cast<const long long *>(src);
+        long long *d8 = reinterpret_cast<long long *>(&ws->S);
+        for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+        wacc_clear(&ws->acc, lane);
+        const long long t0 = clock64();
+        run_job_mixed(ws->S, &ws->acc, J, lane);
+        __syncwarp();
+        if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
+        wacc_flush(&ws->acc, J->totals, lane);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream)
+{
+    const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
+    packets_mixed<<<blocks, threads, sm, stream>>>(jobs, njobs, status);
+    return cudaGetLastError();
+}
+
+int occupancy_mixed(int threads)
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed, threads,
+                                                  (size_t)(threads / 32) * sizeof(WarpShared));
+    return n;
+}
+
+}  // namespace smcrt

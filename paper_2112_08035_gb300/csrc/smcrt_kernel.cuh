@@ -1,0 +1,563 @@
+// smcrt_kernel.cuh -- persistent photon-packet kernel for sm_103a.
+//
+// One thread carries one photon packet; warps pull packet ids from the
+// job's atomic cursor (warp-aggregated: one atomicAdd per refill, ranks
+// from a ballot), so a lane whose packet terminates is refilled at the
+// next iteration and the warp stays full until the job runs dry.
+//
+// Every loop iteration performs exactly ONE full scene SDF evaluation per
+// lane (the dominant cost, Sec. 4 "having to evaluate every SDF each time
+// the photon needs to be moved").  What the lane does with it depends on
+// its phase:
+//   TRACE  evaluate at p: bounding box exit, interaction or sphere-trace
+//          step (Sec. 2.3, Fig. 2 right, Fig. 3; Eq. 1 for tau),
+//   NRM    six probes p +/- h e_a of the nearest surface's SDF: central
+//          differences for the normal (Sec. 1 "numerical differentiation"),
+//   PROJ   (FP64) Newton projection onto the surface along the normal,
+//   FAR    region on the far side of the surface,
+//   NEAR   region on the near side; then Fresnel reflection or Snell
+//          refraction if the refractive index changes (Sec. 2.3).
+// Lanes at an interface therefore share the scene evaluation with lanes
+// that are tracing, instead of running a divergent interface routine.
+//
+// The FP64 instantiation performs the same IEEE operations in the same
+// order as the FP64 reference algorithm (compiled with -fmad=false), with
+// ln and sin/cos written here from textbook series, so its integer tallies
+// are bit-identical to the reference.  The mixed instantiation traces in
+// FP32 and refines interfaces in FP64 only near grazing or critical
+// incidence.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "smcrt_internal.h"
+
+namespace smcrt {
+
+#define SMCRT_FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10, from its definition (Salmon, Moraes, Dror & Shaw, SC'11):
+// ten rounds of two 32x32 -> 64-bit products with multipliers 0xD2511F53 and
+// 0xCD9E8D57, key bumped by the Weyl constants 0x9E3779B9 / 0xBB67AE85.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Packet stream: key (seed lo, seed hi); counter (event, 0, id lo, id hi).
+struct Rng {
+    uint32_t k0, k1, id_lo, id_hi, event;
+    __device__ __forceinline__ uint4 next()
+    {
+        uint4 w = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), k0, k1);
+        event += 1u;
+        return w;
+    }
+};
+
+// Uniforms in (0, 1]: FP64 uses the whole 32-bit word, FP32 its top 24 bits.
+__device__ __forceinline__ double u01_64(uint32_t w) { return ((double)w + 1.0) * (1.0 / 4294967296.0); }
+__device__ __forceinline__ float u01_32(uint32_t w) { return (float)((w >> 8) + 1u) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// FP64 ln and sin/cos(2 pi t), written from the series (not libdevice):
+// ln x = e ln2 + 2 atanh((m-1)/(m+1)) with m in (sqrt(1/2), sqrt(2)], atanh
+// series to s^21; sin/cos by reduction to the nearest quarter turn and the
+// Taylor series of sin to a^17, cos to a^16 on |a| <= pi/4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double ln64(double x)
+{
+    const long long b = __double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    if (m > 1.4142135623730951) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double z = s * s;
+    double t = 1.0 / 21.0;
+    t = t * z + 1.0 / 19.0;
+    t = t * z + 1.0 / 17.0;
+    t = t * z + 1.0 / 15.0;
+    t = t * z + 1.0 / 13.0;
+    t = t * z + 1.0 / 11.0;
+    t = t * z + 1.0 / 9.0;
+    t = t * z + 1.0 / 7.0;
+    t = t * z + 1.0 / 5.0;
+    t = t * z + 1.0 / 3.0;
+    t = t * z + 1.0;
+    return (double)e * 0.6931471805599453 + (2.0 * s) * t;
+}
+
+__device__ __forceinline__ void sincos2pi64(double t, double *sn, double *cs)
+{
+    const double q = floor(t * 4.0 + 0.5);
+    const double f = t - q * 0.25;
+    const double a = f * 6.283185307179586;
+    const double z = a * a;
+    double ps = 1.0 / 355687428096000.0;
+    ps = ps * z - 1.0 / 1307674368000.0;
+    ps = ps * z + 1.0 / 6227020800.0;
+    ps = ps * z - 1.0 / 39916800.0;
+    ps = ps * z + 1.0 / 362880.0;
+    ps = ps * z - 1.0 / 5040.0;
+    ps = ps * z + 1.0 / 120.0;
+    ps = ps * z - 1.0 / 6.0;
+    const double s = a + a * (z * ps);
+    double pc = 1.0 / 20922789888000.0;
+    pc = pc * z - 1.0 / 87178291200.0;
+    pc = pc * z + 1.0 / 479001600.0;
+    pc = pc * z - 1.0 / 3628800.0;
+    pc = pc * z + 1.0 / 40320.0;
+    pc = pc * z - 1.0 / 720.0;
+    pc = pc * z + 1.0 / 24.0;
+    pc = pc * z - 0.5;
+    const double c = 1.0 + z * pc;
+    switch (((int)q) & 3) {
+    case 0: *sn = s; *cs = c; break;
+    case 1: *sn = c; *cs = -s; break;
+    case 2: *sn = -s; *cs = -c; break;
+    default: *sn = -c; *cs = s; break;
+    }
+}
+
+// Fixed point: 2^-32 weight units.  FP64: round half to even like llrint.
+__device__ __forceinline__ long long fx64(double x) { return __double2ll_rn(x * 4294967296.0); }
+// FP32 (x >= 0): integer-only scaling of the float's mantissa, round half up.
+__device__ __forceinline__ long long fx32(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xff);
+    if (e == 0) return 0;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 127 - 23 + 32;  // value = m * 2^(e-150), in 2^-32 units
+    if (sh >= 0) return m << (sh > 62 ? 62 : sh);
+    if (sh < -40) return 0;
+    return (m + (1LL << (-sh - 1))) >> (-sh);
+}
+
+// ---------------------------------------------------------------------------
+// Scene evaluation.  Instr.op packs op | (primitive kind << 8).
+// ---------------------------------------------------------------------------
+struct Eval64 { double dmin, dstar, dsel, dbox; int istar, region; };
+struct Eval32 { float dmin, dstar, dsel, dbox; int istar, region; };
+
+__device__ __forceinline__ double box64(double x, double y, double z, double cx, double cy, double cz,
+                                        double hx, double hy, double hz)
+{
+    const double qx = fabs(x - cx) - hx, qy = fabs(y - cy) - hy, qz = fabs(z - cz) - hz;
+    const double mx = fmax(qx, 0.0), my = fmax(qy, 0.0), mz = fmax(qz, 0.0);
+    const double outside = sqrt(mx * mx + my * my + mz * mz);
+    const double inside = fmin(fmax(qx, fmax(qy, qz)), 0.0);
+    return outside + inside;
+}
+
+__device__ __forceinline__ float box32(float x, float y, float z, float cx, float cy, float cz,
+                                       float hx, float hy, float hz)
+{
+    const float qx = fabsf(x - cx) - hx, qy = fabsf(y - cy) - hy, qz = fabsf(z - cz) - hz;
+    const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+    const float outside = sqrtf(mx * mx + my * my + mz * mz);
+    const float inside = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+    return outside + inside;
+}
+
+__device__ __forceinline__ double prim64(const DevScene &S, int kind, int i, double x, double y, double z)
+{
+    const double *P = S.p64 + 8 * i;
+    if (kind == 0) {
+        const double dx = x - __ldg(P), dy = y - __ldg(P + 1), dz = z - __ldg(P + 2);
+        return sqrt(dx * dx + dy * dy + dz * dz) - __ldg(P + 3);
+    }
+    if (kind == 1)
+        return box64(x, y, z, __ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5));
+    const double pax = x - __ldg(P), pay = y - __ldg(P + 1), paz = z - __ldg(P + 2);
+    const double bax = __ldg(P + 3), bay = __ldg(P + 4), baz = __ldg(P + 5);
+    double t = (pax * bax + pay * bay + paz * baz) / __ldg(P + 7);
+    t = fmin(fmax(t, 0.0), 1.0);
+    const double dx = pax - bax * t, dy = pay - bay * t, dz = paz - baz * t;
+    return sqrt(dx * dx + dy * dy + dz * dz) - __ldg(P + 6);
+}
+
+__device__ __forceinline__ float prim32(const DevScene &S, int kind, int i, float x, float y, float z)
+{
+    const float4 A = __ldg(S.p32 + 2 * i);
+    if (kind == 0) {
+        const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
+        return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
+    }
+    const float4 B = __ldg(S.p32 + 2 * i + 1);
+    if (kind == 1) return box32(x, y, z, A.x, A.y, A.z, B.x, B.y, B.z);
+    const float pax = x - A.x, pay = y - A.y, paz = z - A.z;
+    float t = (pax * B.x + pay * B.y + paz * B.z) * B.w;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float dx = pax - B.x * t, dy = pay - B.y * t, dz = paz - B.z * t;
+    return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
+}
+
+// a = left (earlier) operand, b = right.  Smooth union: polynomial smooth
+// minimum (the SDF literature cited with Fig. 1 e).
+__device__ __forceinline__ double csg64(int op, double a, double b, double k)
+{
+    if (op == 1) return fmin(a, b);
+    if (op == 3) return fmax(a, b);
+    if (op == 4) return fmax(a, -b);
+    double h = 0.5 + 0.5 * (b - a) / k;
+    h = fmin(fmax(h, 0.0), 1.0);
+    const double m = b * (1.0 - h) + a * h;
+    return m - k * h * (1.0 - h);
+}
+
+__device__ __forceinline__ float csg32(int op, float a, float b, float kinv)
+{
+    if (op == 1) return fminf(a, b);
+    if (op == 3) return fmaxf(a, b);
+    if (op == 4) return fmaxf(a, -b);
+    const float k = 1.0f / kinv;
+    float h = 0.5f + 0.5f * (b - a) * kinv;
+    h = fminf(fmaxf(h, 0.f), 1.f);
+    const float m = b + (a - b) * h;
+    return m - k * h * (1.f - h);
+}
+
+// Evaluate instructions [i0, i1) as a register-stack program; when `full`,
+// record every region end (region, d_min, istar, and d of surface `sel`).
+template <bool kFull>
+__device__ __forceinline__ double run_prog64(const DevScene &S, int i0, int i1, double x, double y, double z,
+                                             int sel, Eval64 *E)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
+        const int op = ins.x & 0xff, kind = ins.x >> 8;
+        double v = 0.0;
+        if (ins.y >= 0) v = prim64(S, kind, ins.y, x, y, z);
+        if (op == 0) {
+            s3 = s2; s2 = s1; s1 = s0; s0 = v;
+        } else {
+            const double k = (op == 2) ? __ldg(S.k64 + i) : 0.0;
+            if (ins.y >= 0) {
+                s0 = csg64(op, s0, v, k);
+            } else {
+                s0 = csg64(op, s1, s0, k);
+                s1 = s2; s2 = s3;
+            }
+        }
+        if (kFull && ins.z >= 0) {
+            const double d = s0;
+            if (d < 0.0) E->region = ins.z;
+            const double ad = fabs(d);
+            if (ad < E->dmin) { E->dmin = ad; E->istar = ins.z; E->dstar = d; }
+            if (ins.z == sel) E->dsel = d;
+        }
+    }
+    return s0;
+}
+
+template <bool kFull>
+__device__ __forceinline__ float run_prog32(const DevScene &S, int i0, int i1, float x, float y, float z,
+                                            int sel, Eval32 *E)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int i = i0; i < i1; ++i) {
+        const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
+        const int op = ins.x & 0xff, kind = ins.x >> 8;
+        float v = 0.f;
+        if (ins.y >= 0) v = prim32(S, kind, ins.y, x, y, z);
+        if (op == 0) {
+            s3 = s2; s2 = s1; s1 = s0; s0 = v;
+        } else {
+            const float kinv = __int_as_float(ins.w);
+            if (ins.y >= 0) {
+                s0 = csg32(op, s0, v, kinv);
+            } else {
+                s0 = csg32(op, s1, s0, kinv);
+                s1 = s2; s2 = s3;
+            }
+        }
+        if (kFull && ins.z >= 0) {
+            const float d = s0;
+            if (d < 0.f) E->region = ins.z;
+            const float ad = fabsf(d);
+            if (ad < E->dmin) { E->dmin = ad; E->istar = ins.z; E->dstar = d; }
+            if (ins.z == sel) E->dsel = d;
+        }
+    }
+    return s0;
+}
+
+// Full scene evaluation (Sec. 2.3): every region, then the bounding box.
+__device__ __forceinline__ Eval64 scene_eval64(const DevScene &S, double x, double y, double z, int sel)
+{
+    Eval64 E;
+    E.dmin = __longlong_as_double(0x7ff0000000000000LL);
+    E.dstar = 0.0; E.dsel = 0.0; E.istar = -1; E.region = -1;
+    run_prog64<true>(S, 0, S.ninstr, x, y, z, sel, &E);
+    const double db = box64(x, y, z, S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2]);
+    E.dbox = db;
+    if (fabs(db) < E.dmin) { E.dmin = fabs(db); E.istar = -1; E.dstar = db; }
+    if (sel == -1) E.dsel = db;
+    return E;
+}
+
+__device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float y, float z, int sel)
+{
+    Eval32 E;
+    E.dmin = __int_as_float(0x7f800000);
+    E.dstar = 0.f; E.dsel = 0.f; E.istar = -1; E.region = -1;
+    run_prog32<true>(S, 0, S.ninstr, x, y, z, sel, &E);
+    const float db = box32(x, y, z, S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2]);
+    E.dbox = db;
+    if (fabsf(db) < E.dmin) { E.dmin = fabsf(db); E.istar = -1; E.dstar = db; }
+    if (sel == -1) E.dsel = db;
+    return E;
+}
+
+// SDF of one surface in FP64 (region program, or the bounding box for -1).
+__device__ __forceinline__ double surface64(const DevScene &S, int r, double x, double y, double z)
+{
+    if (r < 0) return box64(x, y, z, S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2]);
+    const int2 rr = __ldg(S.rrange + r);
+    return run_prog64<false>(S, rr.x, rr.y, x, y, z, -2, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Track-length tally (Sec. 3.2): 3D DDA over the grid (Amanatides & Woo
+// 1987), distance to each axis' next plane recomputed from the segment
+// start; each piece adds round(w * piece * 2^32) to its voxel atomically.
+// Per-axis state lives in scalars (no dynamically indexed arrays, which
+// would be placed in local memory); ties advance x before y before z.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void red_add(long long *a, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
+}
+
+// FP64: the reference's arithmetic, operation for operation.
+__device__ __forceinline__ bool clip64(double lo, double hi, double p, double u, double &tin, double &tout)
+{
+    if (u != 0.0) {
+        const double t0 = (lo - p) / u;
+        const double t1 = (hi - p) / u;
+        tin = fmax(tin, fmin(t0, t1));
+        tout = fmin(tout, fmax(t0, t1));
+        return true;
+    }
+    return !(p < lo || p > hi);
+}
+
+__device__ __forceinline__ void dda_axis64(double lo, double dl, int n, double p, double u, double tin, int &i,
+                                           double &tn)
+{
+    const double xa = p + tin * u;
+    const double f = floor((xa - lo) / dl);
+    i = (int)fmin(fmax(f, 0.0), (double)(n - 1));
+    if (u > 0.0)
+        tn = ((lo + (double)(i + 1) * dl) - p) / u;
+    else if (u < 0.0)
+        tn = ((lo + (double)i * dl) - p) / u;
+    else
+        tn = __longlong_as_double(0x7ff0000000000000LL);
+}
+
+static __device__ __noinline__ void tally64(const DevScene &S, long long *flu, double px, double py, double pz,
+                                            double ux, double uy, double uz, double len, double w,
+                                            unsigned *npieces)
+{
+    if (!(len > 0.0) || !(w > 0.0)) return;
+    double tin = 0.0, tout = len;
+    if (!clip64(S.g_lo[0], S.g_hi[0], px, ux, tin, tout)) return;
+    if (!clip64(S.g_lo[1], S.g_hi[1], py, uy, tin, tout)) return;
+    if (!clip64(S.g_lo[2], S.g_hi[2], pz, uz, tin, tout)) return;
+    if (!(tin < tout)) return;
+    const int nx = S.g_n[0], ny = S.g_n[1], nz = S.g_n[2];
+    int ix, iy, iz;
+    double tx, ty, tz;
+    dda_axis64(S.g_lo[0], S.g_dl[0], nx, px, ux, tin, ix, tx);
+    dda_axis64(S.g_lo[1], S.g_dl[1], ny, py, uy, tin, iy, ty);
+    dda_axis64(S.g_lo[2], S.g_dl[2], nz, pz, uz, tin, iz, tz);
+    double t = tin;
+    int guard = nx + ny + nz + 3;
+    while (guard-- > 0) {
+        const int ax = (tx <= ty && tx <= tz) ? 0 : ((ty <= tz) ? 1 : 2);
+        const double ta = ax == 0 ? tx : (ax == 1 ? ty : tz);
+        const double tend = fmin(ta, tout);
+        const double piece = tend - t;
+        if (piece > 0.0) {
+            const long long off = ((long long)iz * ny + iy) * nx + ix;
+            red_add(flu + off, fx64(w * piece));
+            *npieces += 1u;
+            t = tend;
+        }
+        if (ta >= tout) break;
+        if (ax == 0) {
+            ix += ux > 0.0 ? 1 : -1;
+            if (ix < 0 || ix >= nx) break;
+            tx = ux > 0.0 ? ((S.g_lo[0] + (double)(ix + 1) * S.g_dl[0]) - px) / ux
+                          : ((S.g_lo[0] + (double)ix * S.g_dl[0]) - px) / ux;
+        } else if (ax == 1) {
+            iy += uy > 0.0 ? 1 : -1;
+            if (iy < 0 || iy >= ny) break;
+            ty = uy > 0.0 ? ((S.g_lo[1] + (double)(iy + 1) * S.g_dl[1]) - py) / uy
+                          : ((S.g_lo[1] + (double)iy * S.g_dl[1]) - py) / uy;
+        } else {
+            iz += uz > 0.0 ? 1 : -1;
+            if (iz < 0 || iz >= nz) break;
+            tz = uz > 0.0 ? ((S.g_lo[2] + (double)(iz + 1) * S.g_dl[2]) - pz) / uz
+                          : ((S.g_lo[2] + (double)iz * S.g_dl[2]) - pz) / uz;
+        }
+    }
+}
+
+// FP32 (mixed): reciprocal directions, incremental voxel offset.
+__device__ __forceinline__ bool clip32(float lo, float hi, float p, float iu, bool nz_, float &tin, float &tout)
+{
+    if (nz_) {
+        const float t0 = (lo - p) * iu;
+        const float t1 = (hi - p) * iu;
+        tin = fmaxf(tin, fminf(t0, t1));
+        tout = fminf(tout, fmaxf(t0, t1));
+        return true;
+    }
+    return !(p < lo || p > hi);
+}
+
+__device__ __forceinline__ void tally32(const DevScene &S, long long *flu, float px, float py, float pz,
+                                        float ux, float uy, float uz, float len, float w,
+                                        unsigned *npieces)
+{
+    if (!(len > 0.f) || !(w > 0.f)) return;
+    const float iux = 1.0f / ux, iuy = 1.0f / uy, iuz = 1.0f / uz;
+    float tin = 0.f, tout = len;
+    if (!clip32(S.g_lo32[0], S.g_hi32[0], px, iux, ux != 0.f, tin, tout)) return;
+    if (!clip32(S.g_lo32[1], S.g_hi32[1], py, iuy, uy != 0.f, tin, tout)) return;
+    if (!clip32(S.g_lo32[2], S.g_hi32[2], pz, iuz, uz != 0.f, tin, tout)) return;
+    if (!(tin < tout)) return;
+    const int nx = S.g_n[0], ny = S.g_n[1], nz = S.g_n[2];
+    const float inf = __int_as_float(0x7f800000);
+    const float lx = S.g_lo32[0], ly = S.g_lo32[1], lz = S.g_lo32[2];
+    const float dx = S.g_dl32[0], dy = S.g_dl32[1], dz = S.g_dl32[2];
+    int ix = min(max(__float2int_rd((px + tin * ux - lx) * S.g_idl32[0]), 0), nx - 1);
+    int iy = min(max(__float2int_rd((py + tin * uy - ly) * S.g_idl32[1]), 0), ny - 1);
+    int iz = min(max(__float2int_rd((pz + tin * uz - lz) * S.g_idl32[2]), 0), nz - 1);
+    const int sx = ux > 0.f ? 1 : -1, sy = uy > 0.f ? 1 : -1, sz = uz > 0.f ? 1 : -1;
+    float tx = ux != 0.f ? ((lx + (float)(ix + (sx > 0)) * dx) - px) * iux : inf;
+    float ty = uy != 0.f ? ((ly + (float)(iy + (sy > 0)) * dy) - py) * iuy : inf;
+    float tz = uz != 0.f ? ((lz + (float)(iz + (sz > 0)) * dz) - pz) * iuz : inf;
+    long long off = ((long long)iz * ny + iy) * nx + ix;
+    const long long sxy = (long long)nx * ny;
+    float t = tin;
+    int guard = nx + ny + nz + 3;
+    while (guard-- > 0) {
+        const bool bx = tx <= ty && tx <= tz;
+        const bool by = !bx && ty <= tz;
+        const float ta = bx ? tx : (by ? ty : tz);
+        const float tend = fminf(ta, tout);
+        const float piece = tend - t;
+        if (piece > 0.f) {
+            red_add(flu + off, fx32(w * piece));
+            *npieces += 1u;
+            t = tend;
+        }
+        if (ta >= tout) break;
+        if (bx) {
+            ix += sx;
+            if ((unsigned)ix >= (unsigned)nx) break;
+            off += sx;
+            tx = ((lx + (float)(ix + (sx > 0)) * dx) - px) * iux;
+        } else if (by) {
+            iy += sy;
+            if ((unsigned)iy >= (unsigned)ny) break;
+            off += sy > 0 ? nx : -nx;
+            ty = ((ly + (float)(iy + (sy > 0)) * dy) - py) * iuy;
+        } else {
+            iz += sz;
+            if ((unsigned)iz >= (unsigned)nz) break;
+            off += sz > 0 ? sxy : -sxy;
+            tz = ((lz + (float)(iz + (sz > 0)) * dz) - pz) * iuz;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Orthonormal basis perpendicular to a unit vector: branchless construction
+// of Duff et al., "Building an Orthonormal Basis, Revisited", JCGT 2017.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void onb64(double nx, double ny, double nz, double b1[3], double b2[3])
+{
+    const double sg = copysign(1.0, nz);
+    const double a = -1.0 / (sg + nz);
+    const double b = nx * ny * a;
+    b1[0] = 1.0 + sg * nx * nx * a; b1[1] = sg * b; b1[2] = -sg * nx;
+    b2[0] = b; b2[1] = sg + ny * ny * a; b2[2] = -ny;
+}
+
+__device__ __forceinline__ void onb32(float nx, float ny, float nz, float b1[3], float b2[3])
+{
+    const float sg = copysignf(1.f, nz);
+    const float a = -1.f / (sg + nz);
+    const float b = nx * ny * a;
+    b1[0] = 1.f + sg * nx * nx * a; b1[1] = sg * b; b1[2] = -sg * nx;
+    b2[0] = b; b2[1] = sg + ny * ny * a; b2[2] = -ny;
+}
+
+// ---------------------------------------------------------------------------
+// Tally accumulators.  Frequent per-lane counters stay in registers; the
+// rest are summed per warp in shared memory (slot i mirrors the i-th int64
+// of smcrt_totals) and flushed to the job's totals when the warp leaves it.
+// ---------------------------------------------------------------------------
+enum TotSlot {
+    kR = 0, kT, kA, kKilled, kGain, kPackets, kScat, kSteps, kEvals, kIntf, kFres, kPieces, kCap, kRefined,
+    kBusy, kNumSlots = 16
+};
+
+struct WarpAcc {
+    unsigned long long v[kNumSlots];
+};
+
+__device__ __forceinline__ void wadd(WarpAcc *a, int slot, long long x)
+{
+    if (x != 0) atomicAdd(&a->v[slot], (unsigned long long)x);
+}
+
+__device__ __forceinline__ long long warp_sum(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(SMCRT_FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void wacc_clear(WarpAcc *a, int lane)
+{
+    if (lane < kNumSlots) a->v[lane] = 0ull;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void wacc_flush(WarpAcc *a, smcrt_totals *t, int lane)
+{
+    __syncwarp();
+    if (lane < kBusy + 1) {
+        const unsigned long long x = a->v[lane];
+        if (x) red_add(reinterpret_cast<long long *>(t) + lane, (long long)x);
+    }
+    __syncwarp();
+}
+
+enum Phase { kTrace = 0, kNrm = 1, kProj = 2, kFar = 3, kNear = 4, kLaunch = 5 };
+
+constexpr double kWRoulette = 1e-4;   // roulette threshold (MCML convention)
+constexpr double kRouletteM = 10.0;   // survival 1/m, weight x m
+
+}  // namespace smcrt

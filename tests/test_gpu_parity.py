@@ -1,0 +1,238 @@
+"""GPU parity against the FP64 CPU oracle, through the C-ABI.
+
+FP64 mode: the kernel performs the oracle's IEEE operations in the same
+order, so every int64 tally (fluence voxels, R, T, A, killed, gain,
+scatter and step counts) and every per-packet record must be IDENTICAL.
+Mixed mode: a different but consistent estimator of the same transport, so
+R, T, A and the fluence must agree with the oracle within Monte Carlo error
+(z-score over per-packet variances; 4 sigma).
+"""
+import math
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2112_08035_gb300 as smc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FX = 2.0 ** 32
+EXACT_KEYS = ("R", "T", "A", "killed", "gain", "packets", "scatters", "steps")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = smc.Context(0)
+    yield c
+    c.close()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def run_gpu(ctx, wl, precision, records=False, id_begin=0, blocks=0, threads=0, fluence=True):
+    torch = _torch()
+    plan = ctx.plan(wl, precision)
+    if blocks or threads:
+        plan.set_launch(blocks, threads)
+    g = wl.grid
+    flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda") if fluence else None
+    tot = smc.totals_tensor()
+    rec = torch.zeros(wl.npackets * 8, dtype=torch.int64, device="cuda") if records else None
+    plan.launch(id_begin, wl.npackets, wl.seed, flu, tot, rec)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    plan.close()
+    out = (flu.cpu().numpy() if fluence else None, smc.totals_from_tensor(tot))
+    if records:
+        r = rec.cpu().numpy().view(smc.RECORD_DTYPE)
+        out = out + (r,)
+    return out
+
+
+def assert_exact(tg, to):
+    for k in EXACT_KEYS:
+        assert tg[k] == to[k], (k, tg[k], to[k])
+
+
+SMALL = [
+    (W.sphere_pencil, 3000),
+    (W.three_layer_slab, 1500),
+    (W.vessel_network, 300),
+    (W.glass_container, 600),
+]
+
+
+@pytest.mark.parametrize("factory,n", SMALL, ids=[f.__name__ for f, _ in SMALL])
+def test_fp64_bitexact_small(ctx, factory, n):
+    wl = factory().with_packets(n)
+    fo, to, ro = O.run(wl, records=True)
+    fg, tg, rg = run_gpu(ctx, wl, "fp64", records=True)
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+    for f in ("R", "T", "A", "killed", "gain", "scatters", "steps"):
+        assert np.array_equal(rg[f], ro[f]), f
+
+
+def test_fp64_bitexact_config0_full_size(ctx):
+    # the plain-FP64 sphere workload at its full 1e5 packets, 50^3 grid
+    wl = W.sphere_pencil()
+    fo, to, _ = O.run(wl)
+    fg, tg = run_gpu(ctx, wl, "fp64")
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+
+
+def test_fp64_bitexact_ragged_launch_shapes(ctx):
+    # a ragged packet count over several launch shapes: same bits every time
+    wl = W.three_layer_slab(1237, grid_n=33)
+    fo, to, _ = O.run(wl)
+    for blocks, threads in [(1, 32), (3, 64), (5, 96), (0, 128), (152 * 7, 128)]:
+        fg, tg = run_gpu(ctx, wl, "fp64", blocks=blocks, threads=threads)
+        assert_exact(tg, to)
+        assert np.array_equal(fg, fo)
+
+
+def test_fp64_id_offset_and_split_additivity(ctx):
+    wl = W.glass_container(900, grid_n=40)
+    fo, to, _ = O.run(wl, 5000, 5900)
+    fg, tg = run_gpu(ctx, wl, "fp64", id_begin=5000)
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+    fa, ta = run_gpu(ctx, wl.with_packets(400), "fp64", id_begin=5000)
+    fb, tb = run_gpu(ctx, wl.with_packets(500), "fp64", id_begin=5400)
+    assert np.array_equal(fa + fb, fo)
+    for k in EXACT_KEYS:
+        assert ta[k] + tb[k] == to[k]
+
+
+def _zcheck(rg, ro, key, k=4.0):
+    a = rg[key].astype(np.float64) / FX
+    b = ro[key].astype(np.float64) / FX
+    se = math.sqrt(a.var() / a.size + b.var() / b.size)
+    z = abs(a.mean() - b.mean()) / max(se, 1e-12)
+    assert z < k, (key, a.mean(), b.mean(), se, z)
+    return z
+
+
+MIXED = [
+    (W.sphere_pencil, 200_000, 20_000),
+    (W.three_layer_slab, 200_000, 10_000),
+    (W.vessel_network, 40_000, 2_000),
+    (W.glass_container, 100_000, 5_000),
+]
+
+
+@pytest.mark.parametrize("factory,ng,no", MIXED, ids=[f.__name__ for f, _, _ in MIXED])
+def test_mixed_matches_oracle_statistically(ctx, factory, ng, no):
+    wl = factory()
+    fo, to, ro = O.run(wl.with_packets(no), records=True)
+    # disjoint packet ids for the GPU sample: independent estimates
+    fg, tg, rg = run_gpu(ctx, wl.with_packets(ng), "mixed", records=True, id_begin=10_000_000)
+    for key in ("R", "T", "A"):
+        _zcheck(rg, ro, key)
+    # fluence: relative L2 difference of the normalised maps is consistent
+    # with the oracle's own noise (compare against half-sample noise)
+    po = fo / FX / no
+    pg = fg / FX / ng
+    l2 = np.linalg.norm(pg - po) / np.linalg.norm(po)
+    fo1, _, _ = O.run(wl.with_packets(no // 2), 20_000_000)
+    fo2, _, _ = O.run(wl.with_packets(no // 2), 30_000_000)
+    noise = np.linalg.norm(fo1 / (no // 2) - fo2 / (no // 2)) / FX / np.linalg.norm(po) / math.sqrt(2)
+    assert l2 < 2.5 * noise + 1e-3, (l2, noise)
+    # energy closes per packet (FP32 weights: relative 1e-5 per packet)
+    bal = (rg["R"] + rg["T"] + rg["A"] + rg["killed"] - rg["gain"]) / FX
+    assert np.all(np.abs(bal - 1.0) < 1e-4)
+
+
+def test_launch_shape_limits(ctx):
+    plan = ctx.plan(W.sphere_pencil(10), "mixed")
+    for bad in [(0, 256), (0, 33), (-1, 64)]:
+        with pytest.raises(smc.SmcrtError) as e:
+            plan.set_launch(*bad)
+        assert e.value.code == smc.ERR_BAD_ARG
+    plan.close()
+
+
+def test_edge_cases(ctx):
+    wl = W.sphere_pencil(1)
+    # a single packet, both precisions
+    fo, to, _ = O.run(wl)
+    fg, tg = run_gpu(ctx, wl, "fp64")
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+    fg, tg = run_gpu(ctx, wl, "mixed")
+    assert tg["packets"] == 1
+    # zero packets: nothing launched, nothing tallied
+    fg, tg = run_gpu(ctx, wl.with_packets(0), "fp64")
+    assert tg["packets"] == 0 and not fg.any()
+    # no fluence buffer: totals only
+    _, tg = run_gpu(ctx, wl.with_packets(500), "fp64", fluence=False)
+    _, to, _ = O.run(wl.with_packets(500), fluence=False)
+    assert_exact(tg, to)
+    # one voxel grid; source outside the bounding box escapes at once
+    w2 = replace(wl.with_packets(300), grid=W.Grid((-1, -1, -1), (1, 1, 1), (1, 1, 1)))
+    fo, to, _ = O.run(w2)
+    fg, tg = run_gpu(ctx, w2, "fp64")
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+    w3 = replace(wl.with_packets(64), source=W.Source(W.PENCIL, (0, 0, 5.0), (0, 0, -1.0)))
+    fg, tg = run_gpu(ctx, w3, "fp64")
+    assert tg["T"] == 64 * 2 ** 32 and tg["steps"] == 0
+    # step cap of one: every surviving packet is killed after one step
+    w4 = replace(wl.with_packets(200), scene=replace(wl.scene, max_steps=1))
+    fo, to, _ = O.run(w4)
+    fg, tg = run_gpu(ctx, w4, "fp64")
+    assert_exact(tg, to)
+    assert tg["max_steps_hit"] > 0
+
+
+@pytest.mark.parametrize("g", [-0.7, 0.0, 0.99])
+def test_fp64_bitexact_anisotropy_extremes(ctx, g):
+    wl = W.sphere_pencil(800)
+    wl = replace(wl, scene=replace(wl.scene, regions=(replace(wl.scene.regions[0], g=g),)))
+    fo, to, _ = O.run(wl)
+    fg, tg = run_gpu(ctx, wl, "fp64")
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+
+
+def test_fp64_bitexact_iso_source_and_roulette(ctx):
+    # isotropic point source in a high-albedo sphere: long histories and
+    # Russian roulette both occur
+    sc = W.isotropic_sphere(100.0)   # ~5e3 scatterings: weights reach the roulette threshold
+    sc = replace(sc, regions=(replace(sc.regions[0], mu_a=2.0, g=0.5, n=1.4),))
+    wl = W.Workload("iso", sc, W.Source(W.ISO_POINT, (0, 0, 0), (0, 0, -1.0)),
+                    W.Grid((-0.6, -0.6, -0.6), (0.6, 0.6, 0.6), (24, 24, 24)), 300, 77, "fp64")
+    fo, to, _ = O.run(wl)
+    fg, tg = run_gpu(ctx, wl, "fp64")
+    assert to["gain"] > 0 and to["killed"] > 0
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+
+
+def test_full_size_three_layer_sampled(ctx):
+    """The 1e7-packet layered workload in its benchmark launch shape: FP64
+    per-packet records of a random sample of ids equal the oracle's one by
+    one; mixed-mode R/T/A agree with the FP64 run within MC error."""
+    torch = _torch()
+    wl = W.three_layer_slab()
+    fg, tg, rg = run_gpu(ctx, wl, "fp64", records=True)
+    assert tg["packets"] == wl.npackets
+    rng = np.random.default_rng(5)
+    ids = np.sort(rng.choice(wl.npackets, 300, replace=False))
+    for i in ids:
+        _, _, ro = O.run(wl, int(i), int(i) + 1, threads=1, fluence=False, records=True)
+        for f in ("R", "T", "A", "killed", "gain", "scatters", "steps"):
+            assert rg[f][i] == ro[f][0], (i, f)
+    fm, tm, rm = run_gpu(ctx, wl, "mixed", records=True)
+    assert tm["packets"] == wl.npackets
+    for key in ("R", "T", "A"):
+        _zcheck(rm, rg, key)
+    del rg, rm
+    torch.cuda.empty_cache()

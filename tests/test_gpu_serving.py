@@ -1,0 +1,91 @@
+"""Serving: continuously batched jobs through smcrt_submit / poll / wait.
+
+Each packet's history depends only on (seed, packet id) and every tally is
+an int64 sum, so a job's result is the same alone and in any mix: the
+test requires bit-identical fluence and totals (a tolerance of zero)."""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2112_08035_gb300 as smc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("R", "T", "A", "killed", "gain", "packets", "scatters", "steps")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = smc.Context(0)
+    yield c
+    c.close()
+
+
+def _jobs():
+    return [W.sphere_pencil(30_000, 11, "mixed"), W.three_layer_slab(200_000, 12, "mixed", grid_n=64),
+            W.glass_container(50_000, 13, "mixed", grid_n=50), W.vessel_network(5_000, 3, "mixed", grid_n=50),
+            W.sphere_pencil(20_000, 14, "fp64"), W.three_layer_slab(7, 15, "fp64", grid_n=10)]
+
+
+def test_same_result_alone_and_in_the_mix(ctx):
+    jobs = _jobs()
+    alone = [ctx.run(j, j.precision) for j in jobs]
+    ids = [ctx.submit(j) for j in jobs]
+    got = [ctx.wait(i, 300.0) for i in ids]
+    for (fa, ta), (fm, tm, lat), j in zip(alone, got, jobs):
+        assert np.array_equal(fa, fm), j.name
+        for k in KEYS:
+            assert ta[k] == tm[k], (j.name, k)
+        assert lat > 0
+
+
+def test_staggered_arrivals_and_poll(ctx):
+    jobs = _jobs()[:4]
+    ids = []
+    for j in jobs:
+        ids.append(ctx.submit(j))
+        time.sleep(0.01)
+    deadline = time.time() + 300
+    while not all(ctx.poll(i) for i in ids):
+        assert time.time() < deadline
+        time.sleep(0.005)
+    for i, j in zip(ids, jobs):
+        f, t, _ = ctx.wait(i, 1.0)
+        assert t["packets"] == j.npackets
+
+
+def test_cancel_and_errors(ctx):
+    big = W.vessel_network(20_000_000, 3, "mixed", grid_n=32)
+    jid = ctx.submit(big)
+    ctx.cancel(jid)
+    with pytest.raises(smc.SmcrtError) as e:
+        ctx.wait(jid, 300.0)
+    assert e.value.code == smc.ERR_CANCELLED
+    with pytest.raises(smc.SmcrtError) as e:
+        ctx.wait(123456789, 0.0)
+    assert e.value.code == smc.ERR_NOT_FOUND
+    # a zero-packet job completes at once with zero tallies
+    z = ctx.submit(W.sphere_pencil(0, 1, "mixed"))
+    f, t, _ = ctx.wait(z, 10.0)
+    assert t["packets"] == 0 and not f.any()
+    # the server keeps working after a cancellation
+    j = W.sphere_pencil(5_000, 21, "mixed")
+    fa, ta = ctx.run(j, "mixed")
+    f, t, _ = ctx.wait(ctx.submit(j), 60.0)
+    assert np.array_equal(f, fa) and t["A"] == ta["A"]
+
+
+def test_timeout_keeps_job(ctx):
+    big = W.glass_container(3_000_000, 5, "mixed", grid_n=32)
+    jid = ctx.submit(big)
+    try:
+        ctx.wait(jid, 0.0)
+        timed_out = False
+    except smc.SmcrtError as e:
+        assert e.code == smc.ERR_TIMEOUT
+        timed_out = True
+    if timed_out:
+        f, t, _ = ctx.wait(jid, 300.0)
+        assert t["packets"] == big.npackets
