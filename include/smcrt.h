@@ -158,7 +158,7 @@ typedef struct {
     int64_t max_steps_hit;/* packets stopped by the step cap */
     int64_t refined;      /* mixed mode: interfaces refined in FP64 */
     int64_t busy_cycles;  /* SM clock cycles warps spent on this job (summed over warps) */
-    int64_t reserved;
+    int64_t parked;       /* serving: times a packet was parked at a round's time budget */
 } smcrt_totals;
 
 /* Optional per-packet record (debugging and per-packet parity). */
@@ -221,16 +221,23 @@ int smcrt_plan_launch(smcrt_plan *plan, uint64_t id_begin, uint64_t npackets, ui
                       int64_t *fluence_dev, smcrt_totals *totals_dev,
                       smcrt_packet_record *records_dev, void *stream);
 
+/* Register budget of the packet kernel: variant 0, 1, 2 keep 5/4/3 (mixed)
+ * or 4/3/2 (FP64) blocks of 128 threads resident per SM; fewer resident
+ * blocks give each thread more registers (no spilling) at lower occupancy.
+ * Results do not depend on the variant. */
+int smcrt_plan_set_variant(smcrt_plan *plan, int32_t variant);
+
 /* Read back the kernel's device error word for the plan's last launches
  * (0 = none) and clear it. */
 int smcrt_plan_status(smcrt_plan *plan, int32_t *status);
 
-/* Time the candidate launch shapes on a short trial run of this plan and
- * keep the fastest (the choice is cached per scene shape in the context).
- * Trial tallies go to scratch buffers.  *blocks / *threads (may be NULL)
- * receive the choice. */
+/* Time the candidate launch shapes (register-budget variant x threads per
+ * block x resident blocks) on a short trial run of this plan and keep the
+ * fastest; the choice is cached per scene shape in the context and applied
+ * to later plans of the same shape.  Trial tallies go to scratch buffers.
+ * *blocks / *threads / *variant (may be NULL) receive the choice. */
 int smcrt_plan_autotune(smcrt_plan *plan, uint64_t trial_packets, int32_t *blocks,
-                        int32_t *threads);
+                        int32_t *threads, int32_t *variant);
 
 /* ---- one-shot synchronous run ------------------------------------------ */
 

@@ -65,11 +65,11 @@ class Grid(C.Structure):
 
 
 TOTAL_FIELDS = ["R", "T", "A", "killed", "gain", "packets", "scatters", "steps", "scene_evals",
-                "interfaces", "fresnel", "pieces", "max_steps_hit", "refined", "busy_cycles"]
+                "interfaces", "fresnel", "pieces", "max_steps_hit", "refined", "busy_cycles", "parked"]
 
 
 class Totals(C.Structure):
-    _fields_ = [(f, C.c_int64) for f in TOTAL_FIELDS] + [("reserved", C.c_int64)]
+    _fields_ = [(f, C.c_int64) for f in TOTAL_FIELDS]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f in TOTAL_FIELDS}
@@ -119,7 +119,8 @@ def lib():
                 "smcrt_plan_set_launch": (C.c_int, [vp, i32, i32]),
                 "smcrt_plan_launch": (C.c_int, [vp, u64, u64, u64, vp, vp, vp, vp]),
                 "smcrt_plan_status": (C.c_int, [vp, C.POINTER(i32)]),
-                "smcrt_plan_autotune": (C.c_int, [vp, u64, C.POINTER(i32), C.POINTER(i32)]),
+                "smcrt_plan_autotune": (C.c_int, [vp, u64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+                "smcrt_plan_set_variant": (C.c_int, [vp, i32]),
                 "smcrt_run": (C.c_int, [vp, C.POINTER(Scene), C.POINTER(Source), C.POINTER(Grid), u64, u64,
                                         i32, vp, C.POINTER(Totals)]),
                 "smcrt_submit": (C.c_int, [vp, C.POINTER(Scene), C.POINTER(Source), C.POINTER(Grid), u64, u64,
@@ -216,10 +217,15 @@ class Plan:
         _check(lib().smcrt_plan_status(self.h, C.byref(v)), "plan_status")
         return v.value
 
+    def set_variant(self, variant):
+        _check(lib().smcrt_plan_set_variant(self.h, int(variant)), "plan_set_variant")
+
     def autotune(self, trial_packets):
-        b, t = C.c_int32(), C.c_int32()
-        _check(lib().smcrt_plan_autotune(self.h, int(trial_packets), C.byref(b), C.byref(t)), "plan_autotune")
-        return b.value, t.value
+        """Returns the chosen (blocks, threads, variant)."""
+        b, t, v = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().smcrt_plan_autotune(self.h, int(trial_packets), C.byref(b), C.byref(t), C.byref(v)),
+               "plan_autotune")
+        return b.value, t.value, v.value
 
     def close(self):
         if self.h:

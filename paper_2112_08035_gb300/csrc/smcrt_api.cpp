@@ -12,6 +12,8 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -196,7 +198,8 @@ struct smcrt_ctx {
     int sm_count = 0;
     size_t budget = 0;
     std::mutex tune_mu;
-    std::map<uint64_t, std::pair<int, int>> tuned;  // scene shape -> (blocks, threads)
+    struct Tuned { int blocks, threads, variant; };
+    std::map<uint64_t, Tuned> tuned;  // scene shape -> launch shape
 
     // serving
     std::mutex mu;
@@ -222,7 +225,7 @@ struct smcrt_plan {
     JobWork *djobs = nullptr;  // ring of launch descriptors
     int ring = 64, ring_pos = 0;
     int *dstatus = nullptr;
-    int blocks = 0, threads = 0;
+    int blocks = 0, threads = 0, variant = 0;
     size_t cells = 0;
     size_t dbytes = 0;
     uint64_t shape_key = 0;
@@ -230,17 +233,21 @@ struct smcrt_plan {
 
 namespace {
 
-int occupancy(int precision, int threads)
+int occupancy(int precision, int threads, int variant)
 {
-    return precision == SMCRT_FP64 ? occupancy_fp64(threads) : occupancy_mixed(threads);
+    return precision == SMCRT_FP64 ? occupancy_fp64(threads, variant) : occupancy_mixed(threads, variant);
 }
 
 cudaError_t launch_kernel(int precision, JobWork *jobs, int njobs, int *status, int blocks, int threads,
-                          cudaStream_t s)
+                          cudaStream_t s, int variant)
 {
-    return precision == SMCRT_FP64 ? launch_fp64(jobs, njobs, status, blocks, threads, s)
-                                   : launch_mixed(jobs, njobs, status, blocks, threads, s);
+    return precision == SMCRT_FP64 ? launch_fp64(jobs, njobs, status, blocks, threads, s, variant)
+                                   : launch_mixed(jobs, njobs, status, blocks, threads, s, variant);
 }
+
+// Register budgets measured fastest at full size on GB300 (see the design
+// notes): mixed 96 registers x 5 blocks/SM, FP64 146 registers x 3 blocks/SM.
+int default_variant(int precision) { return precision == SMCRT_FP64 ? 1 : 0; }
 
 uint64_t shape_key(const smcrt_scene *sc, int precision, const smcrt_grid *g)
 {
@@ -323,6 +330,7 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     std::unique_ptr<smcrt_plan> pl(new smcrt_plan());
     pl->ctx = ctx;
     pl->precision = precision;
+    pl->variant = default_variant(precision);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return SMCRT_ERR_CUDA;
     if (serving_stream) {
         if (cudaMallocAsync(&pl->dbuf, total, serving_stream) != cudaSuccess) return SMCRT_ERR_NO_MEMORY;
@@ -356,6 +364,7 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     }
     H.delta = sc->delta;
     H.ambient_n = sc->ambient_n;
+    H.ambient_n32 = (float)sc->ambient_n;
     H.delta32 = std::max((float)sc->delta, 64.f * ulp_f32(rmax));
     H.h32 = 32.f * H.delta32;
     H.max_steps = sc->max_steps;
@@ -420,8 +429,9 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tuned.find(pl->shape_key);
         if (it != ctx->tuned.end()) {
-            pl->blocks = it->second.first;
-            pl->threads = it->second.second;
+            pl->blocks = it->second.blocks;
+            pl->threads = it->second.threads;
+            pl->variant = it->second.variant;
         }
     }
     *out = pl.release();
@@ -433,7 +443,7 @@ void default_launch(const smcrt_plan *pl, int &blocks, int &threads)
     threads = pl->threads > 0 ? pl->threads : 128;
     blocks = pl->blocks;
     if (blocks <= 0) {
-        const int occ = std::max(1, occupancy(pl->precision, threads));
+        const int occ = std::max(1, occupancy(pl->precision, threads, pl->variant));
         blocks = pl->ctx->sm_count * occ;
     }
 }
@@ -454,7 +464,7 @@ int plan_launch_impl(smcrt_plan *pl, uint64_t id_begin, uint64_t n, uint64_t see
     JobWork *slot = pl->djobs + pl->ring_pos;
     pl->ring_pos = (pl->ring_pos + 1) % pl->ring;
     if (launch_set_job(slot, jw, s) != cudaSuccess) return SMCRT_ERR_CUDA;
-    if (launch_kernel(pl->precision, slot, 1, pl->dstatus, blocks, threads, s) != cudaSuccess)
+    if (launch_kernel(pl->precision, slot, 1, pl->dstatus, blocks, threads, s, pl->variant) != cudaSuccess)
         return SMCRT_ERR_CUDA;
     return SMCRT_OK;
 }
@@ -488,6 +498,7 @@ struct Job {
     // device resources while admitted
     smcrt_plan *plan = nullptr;
     int64_t *dflu = nullptr;
+    JobDefer *ddefer = nullptr;   // parked-packet lists (two) and their header
     int slot = -1;                // index into the device totals array
     size_t bytes = 0;
     uint64_t cursor = 0;          // next packet id to schedule
@@ -505,6 +516,8 @@ namespace {
 constexpr int kMaxSlots = 64;
 constexpr int kRoundsInFlight = 2;
 constexpr double kRoundSeconds = 0.008;   // target device time of one round
+constexpr double kParkSeconds = 0.004;    // device time a packet may run per round before it is parked
+constexpr unsigned kDeferCap = 65536;     // parked packets per list and job
 
 size_t job_bytes(const smcrt_grid &g)
 {
@@ -520,6 +533,28 @@ void free_job_device(Job &j, cudaStream_t st)
     }
     if (j.dflu) cudaFreeAsync(j.dflu, st);
     j.dflu = nullptr;
+    if (j.ddefer) cudaFreeAsync(j.ddefer, st);
+    j.ddefer = nullptr;
+}
+
+// One allocation: JobDefer header, then its two lists.
+int alloc_defer(Job &j, cudaStream_t st)
+{
+    const size_t hdr = (sizeof(JobDefer) + 255) & ~size_t(255);
+    const size_t bytes = hdr + 2 * sizeof(DeferState) * kDeferCap;
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) return SMCRT_ERR_NO_MEMORY;
+    JobDefer h{};
+    h.buf[0] = (DeferState *)((char *)p + hdr);
+    h.buf[1] = h.buf[0] + kDeferCap;
+    h.cap = kDeferCap;
+    // pageable source: staged before the call returns
+    if (cudaMemcpyAsync(p, &h, sizeof h, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaFreeAsync(p, st);
+        return SMCRT_ERR_CUDA;
+    }
+    j.ddefer = (JobDefer *)p;
+    return SMCRT_OK;
 }
 
 // The scheduler thread.  Each round is one replay of a captured CUDA graph:
@@ -549,34 +584,42 @@ void scheduler(smcrt_ctx *ctx)
     int *h_status = nullptr;
     cudaMallocHost(&h_status, sizeof(int));
     const int threads = 128;
-    const int occ_m = std::max(1, occupancy_mixed(threads)), occ_d = std::max(1, occupancy_fp64(threads));
+    const int occ_m = std::max(1, occupancy_mixed(threads, default_variant(SMCRT_MIXED))),
+              occ_d = std::max(1, occupancy_fp64(threads, default_variant(SMCRT_FP64)));
     const int blocks_m = ctx->sm_count * occ_m, blocks_d = ctx->sm_count * occ_d;
     int clk_khz = 1900000;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, ctx->device);
     // warp-cycles one round can spend (the mixed kernel's resident warps)
     const double round_cycles = (double)blocks_m * (threads / 32) * clk_khz * 1e3 * kRoundSeconds;
+    const long long park_cycles = (long long)(clk_khz * 1e3 * kParkSeconds);
 
     struct Buf {
         JobWork *h_tab = nullptr, *d_tab = nullptr;   // [2 * kMaxSlots]: mixed table, then FP64 table
         smcrt_totals *h_tot = nullptr;                // totals snapshot taken at the end of the round
         cudaGraphExec_t graph = nullptr;
-        cudaEvent_t ev = nullptr;
+        cudaEvent_t ev = nullptr, ev0 = nullptr;
         bool busy = false;
         int64_t idx = -1;
+        int njobs = 0;
+        uint64_t quanta = 0;
+        double t_launch = 0;
     } buf[kRoundsInFlight];
+    const bool trace = std::getenv("SMCRT_TRACE") != nullptr;
     for (auto &b : buf) {
         cudaMallocHost(&b.h_tab, sizeof(JobWork) * 2 * kMaxSlots);
         cudaMalloc(&b.d_tab, sizeof(JobWork) * 2 * kMaxSlots);
         cudaMallocHost(&b.h_tot, sizeof(smcrt_totals) * kMaxSlots);
-        cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+        cudaEventCreate(&b.ev);
+        cudaEventCreate(&b.ev0);
         std::memset(b.h_tab, 0, sizeof(JobWork) * 2 * kMaxSlots);
         cudaGraph_t g;
         cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         cudaMemcpyAsync(b.d_tab, b.h_tab, sizeof(JobWork) * 2 * kMaxSlots, cudaMemcpyHostToDevice, st);
+        launch_round_prologue(b.d_tab, 2 * kMaxSlots, st);
         cudaEventRecord(ev_fork, st);
         cudaStreamWaitEvent(st2, ev_fork, 0);
-        launch_mixed(b.d_tab, kMaxSlots, d_status, blocks_m, threads, st);
-        launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status, blocks_d, threads, st2);
+        launch_mixed(b.d_tab, kMaxSlots, d_status, blocks_m, threads, st, default_variant(SMCRT_MIXED));
+        launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status, blocks_d, threads, st2, default_variant(SMCRT_FP64));
         cudaEventRecord(ev_join, st2);
         cudaStreamWaitEvent(st, ev_join, 0);
         cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
@@ -640,6 +683,7 @@ void scheduler(smcrt_ctx *ctx)
             int rc = build_plan(ctx, &j->scene, &j->source, &j->grid, j->precision, &j->plan, st);
             const size_t fb = (size_t)j->grid.n[0] * j->grid.n[1] * j->grid.n[2] * 8;
             if (rc == SMCRT_OK && cudaMallocAsync(&j->dflu, fb, st) != cudaSuccess) rc = SMCRT_ERR_NO_MEMORY;
+            if (rc == SMCRT_OK) rc = alloc_defer(*j, st);
             j->slot = free_slots.back();
             free_slots.pop_back();
             j->admit_round = issued;     // snapshots of earlier rounds do not describe this job
@@ -664,6 +708,15 @@ void scheduler(smcrt_ctx *ctx)
             cudaEventSynchronize(B.ev);
             B.busy = false;
             completed = B.idx;
+            if (trace) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, B.ev0, B.ev);
+                long long parked = 0;
+                for (auto &j : active) parked += B.h_tot[j->slot].parked;
+                std::fprintf(stderr, "[smcrt] round %lld jobs %d quanta %llu gpu %.3f ms wall %.3f ms parked %lld\n",
+                             (long long)B.idx, B.njobs, (unsigned long long)B.quanta, ms,
+                             1e3 * (now_s() - B.t_launch), parked);
+            }
             cudaMemcpy(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
             std::vector<std::shared_ptr<Job>> still;
             for (auto &j : active) {
@@ -678,8 +731,6 @@ void scheduler(smcrt_ctx *ctx)
                     complete(j, &t, *h_status ? SMCRT_ERR_DEVICE : SMCRT_OK);
                 } else if (drained && is_cancelled(j)) {
                     complete(j, &t, SMCRT_ERR_CANCELLED);
-                } else if (drained && j->cursor >= j->npackets) {
-                    complete(j, &t, SMCRT_ERR_DEVICE);   // ids ran but packets are missing
                 } else {
                     still.push_back(j);
                 }
@@ -696,8 +747,8 @@ void scheduler(smcrt_ctx *ctx)
                     complete(j, nullptr, SMCRT_ERR_CANCELLED);
                     continue;
                 }
-            } else if (j->cursor < j->npackets) {
-                runnable.push_back(j);
+            } else {
+                runnable.push_back(j);   // new ids and/or parked packets
             }
             keep.push_back(j);
         }
@@ -708,14 +759,18 @@ void scheduler(smcrt_ctx *ctx)
         }
         double known = 0;
         int nk = 0;
-        for (auto &j : runnable)
+        int nfresh = 0;
+        for (auto &j : runnable) {
             if (j->cost > 0) { known += j->cost; ++nk; }
-        const double dflt = nk ? known / nk : 4.0e4;
-        const double share = round_cycles / (double)runnable.size();
+            if (j->cursor < j->npackets) ++nfresh;
+        }
+        const double dflt = nk ? known / nk : 2.0e5;
+        const double share = round_cycles / (double)std::max(1, nfresh);
         int nm = 0, nd = 0;
         for (auto &j : runnable) {
             const double c = j->cost > 0 ? j->cost : dflt;
             uint64_t q = (uint64_t)std::max(2048.0, share / c);
+            if (!(j->cost > 0)) q = std::min<uint64_t>(q, 16384);   // unmeasured: a short first quantum
             q = std::min<uint64_t>(q, j->npackets - j->cursor);
             JobWork w{};
             w.next = j->cursor;
@@ -727,11 +782,20 @@ void scheduler(smcrt_ctx *ctx)
             w.records = nullptr;
             w.scene = j->plan->dscene;
             w.cancelled = 0;
+            w.park_cycles = park_cycles;
+            w.defer = j->ddefer;
+            w.defer_in = (int32_t)(issued & 1);
             j->cursor += q;
             j->last_round = issued;
             if (j->precision == SMCRT_FP64) B.h_tab[kMaxSlots + nd++] = w;
             else B.h_tab[nm++] = w;
         }
+        B.njobs = (int)runnable.size();
+        B.quanta = 0;
+        for (int k = 0; k < nm; ++k) B.quanta += B.h_tab[k].end - B.h_tab[k].next;
+        for (int k = 0; k < nd; ++k) B.quanta += B.h_tab[kMaxSlots + k].end - B.h_tab[kMaxSlots + k].next;
+        B.t_launch = now_s();
+        cudaEventRecord(B.ev0, st);
         cudaGraphLaunch(B.graph, st);
         cudaEventRecord(B.ev, st);
         B.busy = true;
@@ -755,6 +819,7 @@ void scheduler(smcrt_ctx *ctx)
     for (auto &b : buf) {
         cudaGraphExecDestroy(b.graph);
         cudaEventDestroy(b.ev);
+        cudaEventDestroy(b.ev0);
         cudaFreeHost(b.h_tab);
         cudaFreeHost(b.h_tot);
         cudaFree(b.d_tab);
@@ -879,6 +944,13 @@ int smcrt_plan_launch(smcrt_plan *pl, uint64_t id_begin, uint64_t npackets, uint
                             (cudaStream_t)stream, blocks, threads);
 }
 
+int smcrt_plan_set_variant(smcrt_plan *pl, int32_t variant)
+{
+    if (!pl || variant < 0 || variant >= kNumVariants) return SMCRT_ERR_BAD_ARG;
+    pl->variant = variant;
+    return SMCRT_OK;
+}
+
 int smcrt_plan_status(smcrt_plan *pl, int32_t *status)
 {
     if (!pl || !status) return SMCRT_ERR_BAD_ARG;
@@ -889,7 +961,8 @@ int smcrt_plan_status(smcrt_plan *pl, int32_t *status)
     return SMCRT_OK;
 }
 
-int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int32_t *threads_out)
+int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int32_t *threads_out,
+                        int32_t *variant_out)
 {
     if (!pl || trial == 0) return SMCRT_ERR_BAD_ARG;
     CU(cudaSetDevice(pl->ctx->device));
@@ -904,33 +977,39 @@ int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bb = 0, bt = 0;
-    const int thread_opts[] = {64, 96, 128};
-    for (int t : thread_opts) {
-        const int occ = occupancy(pl->precision, t);
-        if (occ < 1) continue;
-        for (int mult : {1, 2, 4}) {
-            const int b = pl->ctx->sm_count * occ * mult;
-            float ms_best = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaMemsetAsync(flu, 0, pl->cells * 8, 0);
-                cudaMemsetAsync(tot, 0, sizeof(smcrt_totals), 0);
-                cudaEventRecord(e0, 0);
-                int rc = plan_launch_impl(pl, 0, trial, 12345, flu, tot, nullptr, 0, b, t);
-                cudaEventRecord(e1, 0);
-                if (rc != SMCRT_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-                    cudaFree(flu);
-                    cudaFree(tot);
-                    return SMCRT_ERR_CUDA;
+    int bb = 0, bt = 0, bv = 0;
+    const int thread_opts[] = {64, 128};
+    const int saved_variant = pl->variant;
+    int rc = SMCRT_OK;
+    for (int v = 0; v < kNumVariants && rc == SMCRT_OK; ++v) {
+        pl->variant = v;
+        for (int t : thread_opts) {
+            const int occ = occupancy(pl->precision, t, v);
+            if (occ < 1) continue;
+            for (int mult : {1, 2}) {
+                const int b = pl->ctx->sm_count * occ * mult;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    cudaMemsetAsync(flu, 0, pl->cells * 8, 0);
+                    cudaMemsetAsync(tot, 0, sizeof(smcrt_totals), 0);
+                    cudaEventRecord(e0, 0);
+                    rc = plan_launch_impl(pl, 0, trial, 12345, flu, tot, nullptr, 0, b, t);
+                    cudaEventRecord(e1, 0);
+                    if (rc != SMCRT_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                        rc = SMCRT_ERR_CUDA;
+                        break;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms_best = std::min(ms_best, ms);
                 }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms_best = std::min(ms_best, ms);
-            }
-            if (ms_best < best) {
-                best = ms_best;
-                bb = b;
-                bt = t;
+                if (rc != SMCRT_OK) break;
+                if (ms_best < best) {
+                    best = ms_best;
+                    bb = b;
+                    bt = t;
+                    bv = v;
+                }
             }
         }
     }
@@ -938,14 +1017,20 @@ int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int
     cudaEventDestroy(e1);
     cudaFree(flu);
     cudaFree(tot);
+    if (rc != SMCRT_OK) {
+        pl->variant = saved_variant;
+        return rc;
+    }
     pl->blocks = bb;
     pl->threads = bt;
+    pl->variant = bv;
     {
         std::lock_guard<std::mutex> lk(pl->ctx->tune_mu);
-        pl->ctx->tuned[pl->shape_key] = {bb, bt};
+        pl->ctx->tuned[pl->shape_key] = {bb, bt, bv};
     }
     if (blocks_out) *blocks_out = bb;
     if (threads_out) *threads_out = bt;
+    if (variant_out) *variant_out = bv;
     return SMCRT_OK;
 }
 

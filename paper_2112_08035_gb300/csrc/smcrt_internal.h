@@ -50,6 +50,7 @@ struct DevScene {
     float bbc32[3], bbh32[3];
     double delta, ambient_n;
     float delta32;            // FP32 surface threshold (>= 64 ulp of the scene extent)
+    float ambient_n32;
     float h32;                // FP32 central-difference step for normals
     int64_t max_steps;
     // source
@@ -60,6 +61,25 @@ struct DevScene {
     double g_lo[3], g_hi[3], g_dl[3];
     float g_lo32[3], g_hi32[3], g_dl32[3], g_idl32[3];
     int32_t g_n[3], pad1;
+};
+
+// A packet parked between serving rounds: its complete state at a trace
+// boundary (FP32 values are stored widened, which round-trips exactly), so
+// resuming it later continues the same arithmetic and the same random stream.
+struct DeferState {
+    double p[3], u[3], w, tau;
+    long long pA, pG;
+    uint32_t id_lo, id_hi, event, nsteps, pscat, pad[3];
+};
+
+// Per-job deferral lists, double-buffered by round parity: a round resumes
+// the packets parked in list `in` and parks its own stragglers in 1 - in.
+struct JobDefer {
+    unsigned count[2];
+    unsigned cursor[2];
+    DeferState *buf[2];
+    unsigned cap;
+    unsigned overflow;       // stragglers that found the list full (kept running)
 };
 
 // Work descriptor of one job in a launch.  `next` is the packet-id cursor
@@ -74,20 +94,27 @@ struct JobWork {
     smcrt_packet_record *records; // device, may be null
     const DevScene *scene;        // device
     int32_t cancelled;            // host-set: stop handing out ids
-    int32_t pad;
+    int32_t defer_in;             // list resumed in this launch (0 / 1)
+    JobDefer *defer;              // device, may be null (no parking)
+    long long park_cycles;        // > 0: park a packet after this many SM cycles in the launch
 };
 
 // Kernel status word bits.
 constexpr int kStatusBadJob = 1;
 constexpr int kStatusStackOverflow = 2;
 
-// Launch wrappers, one per translation unit.
+// Launch wrappers, one per translation unit; `variant` selects the register
+// budget of the kernel instantiation (0 .. kNumVariants-1).
+constexpr int kNumVariants = 3;
 cudaError_t launch_fp64(JobWork *jobs, int njobs, int *status, int blocks, int threads,
-                        cudaStream_t stream);
+                        cudaStream_t stream, int variant = 0);
 cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int threads,
-                         cudaStream_t stream);
-int occupancy_fp64(int threads);
-int occupancy_mixed(int threads);
+                         cudaStream_t stream, int variant = 0);
+int occupancy_fp64(int threads, int variant = 0);
+int occupancy_mixed(int threads, int variant = 0);
 cudaError_t launch_set_job(JobWork *dst, const JobWork &v, cudaStream_t stream);
+// Round prologue: for each table entry with a deferral list, zero the
+// resume cursor of its input list and the count of its output list.
+cudaError_t launch_round_prologue(JobWork *jobs, int njobs, cudaStream_t stream);
 
 }  // namespace smcrt

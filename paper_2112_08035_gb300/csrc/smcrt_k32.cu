@@ -52,7 +52,7 @@ __device__ __forceinline__ void scatter32(float &ux, float &uy, float &uz, float
 
 __device__ __forceinline__ float region_n32(const DevScene &S, int r)
 {
-    return r < 0 ? (float)S.ambient_n : __ldg(S.reg32 + 2 * r + 1).x;
+    return r < 0 ? S.ambient_n32 : __ldg(S.reg32 + 2 * r + 1).x;
 }
 
 __device__ __forceinline__ double region_n64(const DevScene &S, int r)
@@ -124,6 +124,7 @@ __device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, i
 struct WarpShared {
     DevScene S;
     WarpAcc acc;
+    JobConst jc;
 };
 
 // One warp works through packet ids of job J until the job's cursor passes
@@ -136,12 +137,9 @@ struct WarpShared {
 //   4 the track-length tally of this iteration's move (one call site),
 //   5 one Philox call serving launch, interaction and Fresnel draws,
 //   6 the consumers: release a packet, scatter (HG + roulette), Fresnel.
-__device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int lane)
+__device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
+                             int lane)
 {
-    long long *const flu = J->fluence;
-    smcrt_packet_record *const recs = J->records;
-    const unsigned long long end = J->end, begin = J->begin;
-    const uint32_t k0 = (uint32_t)J->seed, k1 = (uint32_t)(J->seed >> 32);
     const float delta = S.delta32, hstep = S.h32;
 
     bool alive = false, retired = false;
@@ -151,33 +149,45 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
     int phase = kTrace, sub = 0, istar = -1, reg = -1, rfar = -1;
     int nsteps = 0;
     unsigned pscat = 0, npieces = 0;
-    long long pA = 0, pG = 0, evals = 0;
+    long long pA = 0, pG = 0;
     uint32_t id_lo = 0, id_hi = 0, event = 0;
-
-    auto finish = [&](long long dR, long long dT, long long dK) {
-        wadd(wa, kR, dR); wadd(wa, kT, dT); wadd(wa, kKilled, dK);
-        wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
-        wadd(wa, kPackets, 1);
-        if (recs) {
-            smcrt_packet_record r;
-            r.R = dR; r.T = dT; r.A = pA; r.killed = dK; r.gain = pG;
-            r.scatters = pscat; r.steps = nsteps; r.reserved = 0;
-            const unsigned long long id = ((unsigned long long)id_hi << 32) | id_lo;
-            recs[id - begin] = r;
-        }
-        alive = false;
-    };
-    auto escape = [&]() {
-        const long long v = fx32(w);
-        if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) finish(v, 0, 0);
-        else finish(0, v, 0);
-    };
+    uint32_t t_acq = 0;
 
     for (;;) {
-        // ---- 1. refill
+        // ---- 1. refill: this job's parked packets first, then new ids
         {
+            unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            JobDefer *const dfr = (JobDefer *)jc->dfr;
+            const int din = jc->din;
+            if (need && dfr != nullptr) {
+                const int leader = __ffs(need) - 1;
+                unsigned base = 0u, avail = 0u;
+                if (lane == leader) {
+                    // the counter also counts packets that found the list full
+                    // (they kept running): only the first `cap` entries exist
+                    avail = min(*(volatile unsigned *)&dfr->count[din], dfr->cap);
+                    base = atomicAdd(&dfr->cursor[din], (unsigned)__popc(need));
+                }
+                base = __shfl_sync(SMCRT_FULL, base, leader);
+                avail = __shfl_sync(SMCRT_FULL, avail, leader);
+                if (!alive && !retired) {
+                    const unsigned k = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+                    if (k < avail) {
+                        const DeferState &d = dfr->buf[din][k];
+                        px = (float)d.p[0]; py = (float)d.p[1]; pz = (float)d.p[2];
+                        ux = (float)d.u[0]; uy = (float)d.u[1]; uz = (float)d.u[2];
+                        w = (float)d.w; tau = (float)d.tau;
+                        pA = d.pA; pG = d.pG;
+                        id_lo = d.id_lo; id_hi = d.id_hi; event = d.event;
+                        nsteps = (int)d.nsteps; pscat = d.pscat;
+                        phase = kTrace;
+                        t_acq = (uint32_t)clock();
+                        alive = true;
+                    }
+                }
+                need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            }
             const bool want = !alive && !retired;
-            const unsigned need = __ballot_sync(SMCRT_FULL, want);
             if (need) {
                 const int leader = __ffs(need) - 1;
                 unsigned long long base = 0;
@@ -188,13 +198,14 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
                 base = __shfl_sync(SMCRT_FULL, base, leader);
                 if (want) {
                     const unsigned long long id = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                    if (base == ~0ull || id >= end) {
+                    if (base == ~0ull || id >= jc->end) {
                         retired = true;
                     } else {
                         id_lo = (uint32_t)id;
                         id_hi = (uint32_t)(id >> 32);
                         event = 0u;
                         phase = kLaunch;
+                        t_acq = (uint32_t)clock();
                         alive = true;
                     }
                 }
@@ -216,16 +227,26 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
             ex = qx + e * nx; ey = qy + e * ny; ez = qz + e * nz;
         }
         const Eval32 E = scene_eval32(S, ex, ey, ez, sel);
-        evals += __popc(__ballot_sync(SMCRT_FULL, alive && phase != kLaunch));
+        {
+            const unsigned ev = __ballot_sync(SMCRT_FULL, alive && phase != kLaunch);
+            if (lane == 0) wadd(wa, kEvals, __popc(ev));
+        }
 
         // ---- 3. classify
         bool move = false, fresnel = false, iter_done = false;
+        bool fin = false;                      // the packet ends this iteration
+        long long fin_R = 0, fin_T = 0, fin_K = 0;
         float L = 0.f;
         int rnear = -1;
         if (alive) {
             if (phase == kTrace) {
                 if (E.dbox > 0.f) {
-                    escape();
+                    {                                          // leaves the volume: R or T
+                        const long long v = fx32(w);
+                        if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
+                        fin = true;
+                        alive = false;
+                    }
                 } else {
                     reg = E.region;
                     if (E.dmin < delta) {
@@ -260,7 +281,12 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
                         L = delta;                  // forced step along u
                         move = true;
                     } else if (istar < 0) {
-                        escape();
+                        {                                          // leaves the volume: R or T
+                        const long long v = fx32(w);
+                        if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
+                        fin = true;
+                        alive = false;
+                    }
                     } else {
                         wadd(wa, kIntf, 1);
                         qx = px - dstar * nx; qy = py - dstar * ny; qz = pz - dstar * nz;
@@ -293,6 +319,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
             }
             interact = mu_t > 0.f && tau < mu_t * L;
             const float seg = interact ? tau * imu_t : L;
+            long long *const flu = (long long *)jc->flu;
             if (flu) tally32(S, flu, px, py, pz, ux, uy, uz, seg, w, &npieces);
             px += seg * ux; py += seg * uy; pz += seg * uz;
             tau -= mu_t * seg;
@@ -304,7 +331,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
         const bool draws = alive && (phase == kLaunch || interact || fresnel);
         uint4 r = make_uint4(0u, 0u, 0u, 0u);
         if (__any_sync(SMCRT_FULL, draws)) {
-            r = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), k0, k1);
+            r = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), jc->k0, jc->k1);
             if (draws) event += 1u;
         }
 
@@ -353,7 +380,9 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
                     pG += fx32(w * (float)(kRouletteM - 1.0));
                     w = w * (float)kRouletteM;
                 } else {
-                    finish(0, 0, fx32(w));
+                    fin_K = fx32(w);
+                    fin = true;
+                    alive = false;
                 }
             }
         }
@@ -396,18 +425,52 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, JobWork *J, int la
             nsteps += 1;
             if (nsteps >= S.max_steps) {
                 wadd(wa, kCap, 1);
-                finish(0, 0, fx32(w));
+                fin_K = fx32(w);
+                fin = true;
+                alive = false;
+            }
+        }
+        // ---- a terminated packet: one bookkeeping site per iteration
+        if (fin) {
+            wadd(wa, kR, fin_R); wadd(wa, kT, fin_T); wadd(wa, kKilled, fin_K);
+            wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
+            wadd(wa, kPackets, 1);
+            smcrt_packet_record *const recs = (smcrt_packet_record *)jc->recs;
+            if (recs) {
+                smcrt_packet_record r;
+                r.R = fin_R; r.T = fin_T; r.A = pA; r.killed = fin_K; r.gain = pG;
+                r.scatters = pscat; r.steps = nsteps; r.reserved = 0;
+                const unsigned long long id = ((unsigned long long)id_hi << 32) | id_lo;
+                recs[id - jc->begin] = r;
+            }
+        }
+        // ---- park a straggler at a trace boundary (serving rounds only)
+        if (alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
+            JobDefer *const dfr = (JobDefer *)jc->dfr;
+            const int din = jc->din;
+            const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);
+            if (k < dfr->cap) {
+                DeferState &d = dfr->buf[1 - din][k];
+                d.p[0] = px; d.p[1] = py; d.p[2] = pz;
+                d.u[0] = ux; d.u[1] = uy; d.u[2] = uz;
+                d.w = w; d.tau = tau;
+                d.pA = pA; d.pG = pG;
+                d.id_lo = id_lo; d.id_hi = id_hi; d.event = event;
+                d.nsteps = (uint32_t)nsteps; d.pscat = pscat;
+                wadd(wa, kParked, 1);
+                alive = false;
+            } else {
+                atomicAdd(&dfr->overflow, 1u);
+                t_acq = (uint32_t)clock() + 0x7fffffffu;   // list full: run on (one retry per ~1 s)
             }
         }
     }
     const long long pc = warp_sum((long long)npieces);
-    if (lane == 0) {
-        wadd(wa, kPieces, pc);
-        wadd(wa, kEvals, evals);
-    }
+    if (lane == 0) wadd(wa, kPieces, pc);
 }
 
-__global__ void __launch_bounds__(128, 5) packets_mixed(JobWork *jobs, int njobs, int *status)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, int njobs, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -422,10 +485,17 @@ __global__ void __launch_bounds__(128, 5) packets_mixed(JobWork *jobs, int njobs
             e = J->end;
             src = J->scene;
         }
+        int parked = 0;
+        if (lane == 0 && J->defer != nullptr) {
+            const int in = J->defer_in & 1;
+            parked = min(*(volatile unsigned *)&J->defer->count[in], J->defer->cap) >
+                     *(volatile unsigned *)&J->defer->cursor[in];
+        }
         nxt = __shfl_sync(SMCRT_FULL, nxt, 0);
         e = __shfl_sync(SMCRT_FULL, e, 0);
+        parked = __shfl_sync(SMCRT_FULL, parked, 0);
         src = (const DevScene *)__shfl_sync(SMCRT_FULL, (unsigned long long)src, 0);
-        if (nxt >= e) continue;
+        if (nxt >= e && !parked) continue;
         if (src == nullptr || J->totals == nullptr) {
             if (lane == 0) atomicOr(status, kStatusBadJob);
             continue;
@@ -433,9 +503,10 @@ __global__ void __launch_bounds__(128, 5) packets_mixed(JobWork *jobs, int njobs
         const long long *s8 = reinterpret_cast<const long long *>(src);
         long long *d8 = reinterpret_cast<long long *>(&ws->S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+        if (lane == 0) jobconst_fill(&ws->jc, J);
         wacc_clear(&ws->acc, lane);
         const long long t0 = clock64();
-        run_job_mixed(ws->S, &ws->acc, J, lane);
+        run_job_mixed(ws->S, &ws->acc, &ws->jc, J, lane);
         __syncwarp();
         if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
         wacc_flush(&ws->acc, J->totals, lane);
@@ -444,18 +515,32 @@ __global__ void __launch_bounds__(128, 5) packets_mixed(JobWork *jobs, int njobs
 
 }  // namespace
 
-cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream)
+// Register budgets of the instantiations: variant v keeps kMinBlocks
+// blocks of 128 threads resident per SM (more blocks = fewer registers per
+// thread, possibly spilled); the autotuner picks per scene.
+constexpr int kVariantBlocks[kNumVariants] = {5, 4, 3};
+
+cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream,
+                        int variant)
 {
     const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
-    packets_mixed<<<blocks, threads, sm, stream>>>(jobs, njobs, status);
+    switch (variant) {
+    case 1: packets_mixed<4><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 2: packets_mixed<3><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    default: packets_mixed<5><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    }
     return cudaGetLastError();
 }
 
-int occupancy_mixed(int threads)
+int occupancy_mixed(int threads, int variant)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed, threads,
-                                                  (size_t)(threads / 32) * sizeof(WarpShared));
+    const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
+    switch (variant) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<4>, threads, sm); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<3>, threads, sm); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<5>, threads, sm); break;
+    }
     return n;
 }
 

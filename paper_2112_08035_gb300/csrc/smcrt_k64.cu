@@ -53,6 +53,7 @@ __device__ __forceinline__ double region_n64(const DevScene &S, int r)
 struct WarpShared {
     DevScene S;
     WarpAcc acc;
+    JobConst jc;
 };
 
 // Same iteration structure as the mixed kernel (refill, one scene
@@ -60,12 +61,9 @@ struct WarpShared {
 // every floating-point operation the reference algorithm's, in its order:
 // the oracle's run of a packet is a sequence of the same IEEE operations on
 // the same values, so its tallies come out bit for bit.
-__device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lane)
+__device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
+                             int lane)
 {
-    long long *const flu = J->fluence;
-    smcrt_packet_record *const recs = J->records;
-    const unsigned long long end = J->end, begin = J->begin;
-    const uint32_t k0 = (uint32_t)J->seed, k1 = (uint32_t)(J->seed >> 32);
     const double delta = S.delta;
 
     bool alive = false, retired = false;
@@ -75,33 +73,45 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
     int phase = kTrace, sub = 0, istar = -1, reg = -1, rfar = -1;
     int nsteps = 0;
     unsigned pscat = 0, npieces = 0;
-    long long pA = 0, pG = 0, evals = 0;
+    long long pA = 0, pG = 0;
     uint32_t id_lo = 0, id_hi = 0, event = 0;
-
-    auto finish = [&](long long dR, long long dT, long long dK) {
-        wadd(wa, kR, dR); wadd(wa, kT, dT); wadd(wa, kKilled, dK);
-        wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
-        wadd(wa, kPackets, 1);
-        if (recs) {
-            smcrt_packet_record r;
-            r.R = dR; r.T = dT; r.A = pA; r.killed = dK; r.gain = pG;
-            r.scatters = pscat; r.steps = nsteps; r.reserved = 0;
-            const unsigned long long id = ((unsigned long long)id_hi << 32) | id_lo;
-            recs[id - begin] = r;
-        }
-        alive = false;
-    };
-    auto escape = [&]() {
-        const long long v = fx64(w);
-        if (ux * S.src_dir[0] + uy * S.src_dir[1] + uz * S.src_dir[2] < 0.0) finish(v, 0, 0);
-        else finish(0, v, 0);
-    };
+    uint32_t t_acq = 0;
 
     for (;;) {
-        // ---- 1. refill
+        // ---- 1. refill: this job's parked packets first, then new ids
         {
+            unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            JobDefer *const dfr = (JobDefer *)jc->dfr;
+            const int din = jc->din;
+            if (need && dfr != nullptr) {
+                const int leader = __ffs(need) - 1;
+                unsigned base = 0u, avail = 0u;
+                if (lane == leader) {
+                    // the counter also counts packets that found the list full
+                    // (they kept running): only the first `cap` entries exist
+                    avail = min(*(volatile unsigned *)&dfr->count[din], dfr->cap);
+                    base = atomicAdd(&dfr->cursor[din], (unsigned)__popc(need));
+                }
+                base = __shfl_sync(SMCRT_FULL, base, leader);
+                avail = __shfl_sync(SMCRT_FULL, avail, leader);
+                if (!alive && !retired) {
+                    const unsigned k = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+                    if (k < avail) {
+                        const DeferState &d = dfr->buf[din][k];
+                        px = (double)d.p[0]; py = (double)d.p[1]; pz = (double)d.p[2];
+                        ux = (double)d.u[0]; uy = (double)d.u[1]; uz = (double)d.u[2];
+                        w = (double)d.w; tau = (double)d.tau;
+                        pA = d.pA; pG = d.pG;
+                        id_lo = d.id_lo; id_hi = d.id_hi; event = d.event;
+                        nsteps = (int)d.nsteps; pscat = d.pscat;
+                        phase = kTrace;
+                        t_acq = (uint32_t)clock();
+                        alive = true;
+                    }
+                }
+                need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            }
             const bool want = !alive && !retired;
-            const unsigned need = __ballot_sync(SMCRT_FULL, want);
             if (need) {
                 const int leader = __ffs(need) - 1;
                 unsigned long long base = 0;
@@ -112,13 +122,14 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
                 base = __shfl_sync(SMCRT_FULL, base, leader);
                 if (want) {
                     const unsigned long long id = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                    if (base == ~0ull || id >= end) {
+                    if (base == ~0ull || id >= jc->end) {
                         retired = true;
                     } else {
                         id_lo = (uint32_t)id;
                         id_hi = (uint32_t)(id >> 32);
                         event = 0u;
                         phase = kLaunch;
+                        t_acq = (uint32_t)clock();
                         alive = true;
                     }
                 }
@@ -144,15 +155,25 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
             ex = qx - ee * nx; ey = qy - ee * ny; ez = qz - ee * nz;
         }
         const Eval64 E = scene_eval64(S, ex, ey, ez, sel);
-        evals += __popc(__ballot_sync(SMCRT_FULL, alive && phase != kLaunch));
+        {
+            const unsigned ev = __ballot_sync(SMCRT_FULL, alive && phase != kLaunch);
+            if (lane == 0) wadd(wa, kEvals, __popc(ev));
+        }
 
         // ---- 3. classify
         bool move = false, fresnel = false, iter_done = false;
+        bool fin = false;                      // the packet ends this iteration
+        long long fin_R = 0, fin_T = 0, fin_K = 0;
         double L = 0.0, R = 1.0, ct = 0.0, n1 = 0.0, n2 = 0.0;
         if (alive) {
             if (phase == kTrace) {
                 if (E.dbox > 0.0) {                      // outside the volume of interest
-                    escape();
+                    {                                          // leaves the volume: R or T
+                        const long long v = fx64(w);
+                        if (ux * S.src_dir[0] + uy * S.src_dir[1] + uz * S.src_dir[2] < 0.0) fin_R = v; else fin_T = v;
+                        fin = true;
+                        alive = false;
+                    }
                 } else {
                     reg = E.region;
                     if (E.dmin < delta) {                // on a boundary: find its normal
@@ -187,7 +208,12 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
                         L = delta;                       // forced step along u
                         move = true;
                     } else if (istar < 0) {
-                        escape();                        // outward through the bounding box
+                        {                                          // leaves the volume: R or T
+                        const long long v = fx64(w);
+                        if (ux * S.src_dir[0] + uy * S.src_dir[1] + uz * S.src_dir[2] < 0.0) fin_R = v; else fin_T = v;
+                        fin = true;
+                        alive = false;
+                    }                        // outward through the bounding box
                     } else {
                         wadd(wa, kIntf, 1);
                         qx = px; qy = py; qz = pz;
@@ -236,6 +262,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
             if (reg >= 0) mu_t = __ldg(S.reg64 + 8 * reg + 4);
             interact = mu_t > 0.0 && tau < mu_t * L;
             const double seg = interact ? tau / mu_t : L;
+            long long *const flu = (long long *)jc->flu;
             if (flu) tally64(S, flu, px, py, pz, ux, uy, uz, seg, w, &npieces);
             px = px + seg * ux; py = py + seg * uy; pz = pz + seg * uz;
             if (!interact) tau = tau - mu_t * L;
@@ -247,7 +274,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
         const bool draws = alive && (phase == kLaunch || interact || (fresnel && R < 1.0));
         uint4 r = make_uint4(0u, 0u, 0u, 0u);
         if (__any_sync(SMCRT_FULL, draws)) {
-            r = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), k0, k1);
+            r = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), jc->k0, jc->k1);
             if (draws) event += 1u;
         }
 
@@ -295,7 +322,9 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
                     pG += fx64(w * (kRouletteM - 1.0));
                     w = w * kRouletteM;
                 } else {
-                    finish(0, 0, fx64(w));
+                    fin_K = fx64(w);
+                    fin = true;
+                    alive = false;
                 }
             }
             tau = -ln64(u01_64(r.w));
@@ -322,18 +351,52 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, JobWork *J, int lan
             nsteps += 1;
             if (nsteps >= S.max_steps) {
                 wadd(wa, kCap, 1);
-                finish(0, 0, fx64(w));
+                fin_K = fx64(w);
+                fin = true;
+                alive = false;
+            }
+        }
+        // ---- a terminated packet: one bookkeeping site per iteration
+        if (fin) {
+            wadd(wa, kR, fin_R); wadd(wa, kT, fin_T); wadd(wa, kKilled, fin_K);
+            wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
+            wadd(wa, kPackets, 1);
+            smcrt_packet_record *const recs = (smcrt_packet_record *)jc->recs;
+            if (recs) {
+                smcrt_packet_record r;
+                r.R = fin_R; r.T = fin_T; r.A = pA; r.killed = fin_K; r.gain = pG;
+                r.scatters = pscat; r.steps = nsteps; r.reserved = 0;
+                const unsigned long long id = ((unsigned long long)id_hi << 32) | id_lo;
+                recs[id - jc->begin] = r;
+            }
+        }
+        // ---- park a straggler at a trace boundary (serving rounds only)
+        if (alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
+            JobDefer *const dfr = (JobDefer *)jc->dfr;
+            const int din = jc->din;
+            const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);
+            if (k < dfr->cap) {
+                DeferState &d = dfr->buf[1 - din][k];
+                d.p[0] = px; d.p[1] = py; d.p[2] = pz;
+                d.u[0] = ux; d.u[1] = uy; d.u[2] = uz;
+                d.w = w; d.tau = tau;
+                d.pA = pA; d.pG = pG;
+                d.id_lo = id_lo; d.id_hi = id_hi; d.event = event;
+                d.nsteps = (uint32_t)nsteps; d.pscat = pscat;
+                wadd(wa, kParked, 1);
+                alive = false;
+            } else {
+                atomicAdd(&dfr->overflow, 1u);
+                t_acq = (uint32_t)clock() + 0x7fffffffu;   // list full: run on (one retry per ~1 s)
             }
         }
     }
     const long long pc = warp_sum((long long)npieces);
-    if (lane == 0) {
-        wadd(wa, kPieces, pc);
-        wadd(wa, kEvals, evals);
-    }
+    if (lane == 0) wadd(wa, kPieces, pc);
 }
 
-__global__ void __launch_bounds__(128, 4) packets_fp64(JobWork *jobs, int njobs, int *status)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) packets_fp64(JobWork *jobs, int njobs, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -348,10 +411,17 @@ __global__ void __launch_bounds__(128, 4) packets_fp64(JobWork *jobs, int njobs,
             e = J->end;
             src = J->scene;
         }
+        int parked = 0;
+        if (lane == 0 && J->defer != nullptr) {
+            const int in = J->defer_in & 1;
+            parked = min(*(volatile unsigned *)&J->defer->count[in], J->defer->cap) >
+                     *(volatile unsigned *)&J->defer->cursor[in];
+        }
         nxt = __shfl_sync(SMCRT_FULL, nxt, 0);
         e = __shfl_sync(SMCRT_FULL, e, 0);
+        parked = __shfl_sync(SMCRT_FULL, parked, 0);
         src = (const DevScene *)__shfl_sync(SMCRT_FULL, (unsigned long long)src, 0);
-        if (nxt >= e) continue;
+        if (nxt >= e && !parked) continue;
         if (src == nullptr || J->totals == nullptr) {
             if (lane == 0) atomicOr(status, kStatusBadJob);
             continue;
@@ -359,9 +429,10 @@ __global__ void __launch_bounds__(128, 4) packets_fp64(JobWork *jobs, int njobs,
         const long long *s8 = reinterpret_cast<const long long *>(src);
         long long *d8 = reinterpret_cast<long long *>(&ws->S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+        if (lane == 0) jobconst_fill(&ws->jc, J);
         wacc_clear(&ws->acc, lane);
         const long long t0 = clock64();
-        run_job_fp64(ws->S, &ws->acc, J, lane);
+        run_job_fp64(ws->S, &ws->acc, &ws->jc, J, lane);
         __syncwarp();
         if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
         wacc_flush(&ws->acc, J->totals, lane);
@@ -370,18 +441,32 @@ __global__ void __launch_bounds__(128, 4) packets_fp64(JobWork *jobs, int njobs,
 
 }  // namespace
 
-cudaError_t launch_fp64(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream)
+// Register budgets of the instantiations: variant v keeps kMinBlocks
+// blocks of 128 threads resident per SM (more blocks = fewer registers per
+// thread, possibly spilled); the autotuner picks per scene.
+constexpr int kVariantBlocks[kNumVariants] = {4, 3, 2};
+
+cudaError_t launch_fp64(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream,
+                        int variant)
 {
     const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
-    packets_fp64<<<blocks, threads, sm, stream>>>(jobs, njobs, status);
+    switch (variant) {
+    case 1: packets_fp64<3><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 2: packets_fp64<2><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    default: packets_fp64<4><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    }
     return cudaGetLastError();
 }
 
-int occupancy_fp64(int threads)
+int occupancy_fp64(int threads, int variant)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64, threads,
-                                                  (size_t)(threads / 32) * sizeof(WarpShared));
+    const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
+    switch (variant) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<3>, threads, sm); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<2>, threads, sm); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<4>, threads, sm); break;
+    }
     return n;
 }
 

@@ -520,7 +520,7 @@ __device__ __forceinline__ void onb32(float nx, float ny, float nz, float b1[3],
 // ---------------------------------------------------------------------------
 enum TotSlot {
     kR = 0, kT, kA, kKilled, kGain, kPackets, kScat, kSteps, kEvals, kIntf, kFres, kPieces, kCap, kRefined,
-    kBusy, kNumSlots = 16
+    kBusy, kParked, kNumSlots = 16
 };
 
 struct WarpAcc {
@@ -548,11 +548,35 @@ __device__ __forceinline__ void wacc_clear(WarpAcc *a, int lane)
 __device__ __forceinline__ void wacc_flush(WarpAcc *a, smcrt_totals *t, int lane)
 {
     __syncwarp();
-    if (lane < kBusy + 1) {
+    if (lane < kNumSlots) {
         const unsigned long long x = a->v[lane];
         if (x) red_add(reinterpret_cast<long long *>(t) + lane, (long long)x);
     }
     __syncwarp();
+}
+
+// Per-job constants of the warp's current job, kept in shared memory and
+// read where used (volatile), so they do not occupy registers across the
+// packet loop.
+struct JobConst {
+    unsigned long long flu, recs, end, begin, dfr;
+    uint32_t k0, k1;
+    int32_t din;
+    uint32_t budget;          // park after this many clock() cycles (0 = never)
+};
+
+__device__ __forceinline__ void jobconst_fill(volatile JobConst *jc, const JobWork *J)
+{
+    jc->flu = (unsigned long long)J->fluence;
+    jc->recs = (unsigned long long)J->records;
+    jc->end = J->end;
+    jc->begin = J->begin;
+    jc->dfr = (unsigned long long)J->defer;
+    jc->k0 = (uint32_t)J->seed;
+    jc->k1 = (uint32_t)(J->seed >> 32);
+    jc->din = J->defer_in & 1;
+    const long long b = J->defer != nullptr ? J->park_cycles : 0;
+    jc->budget = (uint32_t)(b > 0x7fffffffLL ? 0x7fffffffLL : (b < 0 ? 0 : b));
 }
 
 enum Phase { kTrace = 0, kNrm = 1, kProj = 2, kFar = 3, kNear = 4, kLaunch = 5 };

@@ -150,6 +150,49 @@ def test_mixed_matches_oracle_statistically(ctx, factory, ng, no):
     assert np.all(np.abs(bal - 1.0) < 1e-4)
 
 
+def test_register_variants_identical(ctx):
+    # the register budget changes occupancy, never arithmetic
+    wl = W.glass_container(700, grid_n=32)
+    fo, to, _ = O.run(wl)
+    ref = None
+    for v in range(3):
+        plan = ctx.plan(wl, "fp64")
+        plan.set_variant(v)
+        torch = _torch()
+        flu = torch.zeros((32, 32, 32), dtype=torch.int64, device="cuda")
+        tot = smc.totals_tensor()
+        plan.launch(0, wl.npackets, wl.seed, flu, tot)
+        torch.cuda.synchronize()
+        assert np.array_equal(flu.cpu().numpy(), fo)
+        assert_exact(smc.totals_from_tensor(tot), to)
+        plan.close()
+        pm = ctx.plan(wl.with_packets(20000), "mixed")
+        pm.set_variant(v)
+        flu.zero_(); tot.zero_()
+        pm.launch(0, 20000, wl.seed, flu, tot)
+        torch.cuda.synchronize()
+        got = (flu.cpu().numpy(), smc.totals_from_tensor(tot))
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got[0], ref[0])
+            for k in EXACT_KEYS:
+                assert got[1][k] == ref[1][k], (v, k)
+        pm.close()
+    with pytest.raises(smc.SmcrtError):
+        ctx.plan(wl, "mixed").set_variant(3)
+
+
+def test_autotune_choice_is_valid(ctx):
+    wl = W.three_layer_slab(50_000)
+    plan = ctx.plan(wl, "mixed")
+    blocks, threads, variant = plan.autotune(20_000)
+    assert blocks >= 152 and threads in (64, 128) and variant in (0, 1, 2)
+    fg, tg = run_gpu(ctx, wl, "mixed")   # a new plan of the same shape reuses the choice
+    assert tg["packets"] == wl.npackets
+    plan.close()
+
+
 def test_launch_shape_limits(ctx):
     plan = ctx.plan(W.sphere_pencil(10), "mixed")
     for bad in [(0, 256), (0, 33), (-1, 64)]:

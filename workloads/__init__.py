@@ -60,7 +60,7 @@ class Scene:
     bbox_lo: Tuple[float, float, float]
     bbox_hi: Tuple[float, float, float]
     delta: float = 1e-6
-    max_steps: int = 1_000_000
+    max_steps: int = 100_000
 
 
 @dataclass(frozen=True)
