@@ -239,6 +239,40 @@ int smcrt_plan_status(smcrt_plan *plan, int32_t *status);
 int smcrt_plan_autotune(smcrt_plan *plan, uint64_t trial_packets, int32_t *blocks,
                         int32_t *threads, int32_t *variant);
 
+/* ---- launch without device allocation ---------------------------------- */
+
+/* The packet launch of smcrt_plan_launch, for callers that must not
+ * allocate device memory: for example a host application whose own memory
+ * pool reserves the device up front and forbids other cudaMalloc calls, or
+ * a latency-critical loop in which an allocation (which can synchronise the
+ * device) is not allowed.  The paper has no counterpart; this is a property
+ * of the library's interface, not of the method.
+ *
+ * Needs no context: it runs on the current CUDA device and on `stream` (a
+ * cudaStream_t, NULL = legacy default stream), asynchronously.  All the
+ * scratch it needs -- the compiled scene, the launch descriptor and the
+ * kernel's status word -- lives in one fixed device array of 64 KiB inside
+ * the library, held by every device that loads the library until the process
+ * exits.  Scenes are limited accordingly: at most 128 primitives, 256 CSG
+ * nodes and 16 regions (larger ones return SMCRT_ERR_NO_MEMORY; invalid ones
+ * SMCRT_ERR_BAD_SCENE or SMCRT_ERR_BAD_ARG).  It calls no cudaMalloc or
+ * cudaFree and allocates no host memory.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array and leaves its contents
+ * behind: the status word is cleared by each call, the rest is overwritten.
+ * Calls whose work overlaps on the GPU race on the array -- order them on one
+ * stream or wait between them.
+ *
+ * Arguments as smcrt_plan_launch: packets [id_begin, id_begin + npackets)
+ * with key `seed`; fluence_dev (may be NULL) and totals_dev are device
+ * pointers the results are ACCUMULATED into (zero them first).  Results are
+ * identical to a plan launch of the same scene, ids and seed. */
+int smcrt_run_noalloc(const smcrt_scene *scene, const smcrt_source *source, const smcrt_grid *grid,
+                      uint64_t id_begin, uint64_t npackets, uint64_t seed, int32_t precision,
+                      int64_t *fluence_dev, smcrt_totals *totals_dev, void *stream);
+
 /* ---- one-shot synchronous run ------------------------------------------ */
 
 /* Plan, launch and wait: packets [0, npackets), key `seed`.  fluence_out

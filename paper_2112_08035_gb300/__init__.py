@@ -130,6 +130,8 @@ def lib():
                 "smcrt_cancel": (C.c_int, [vp, u64]),
                 "smcrt_serving_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                                   C.POINTER(C.c_int64)]),
+                "smcrt_run_noalloc": (C.c_int, [C.POINTER(Scene), C.POINTER(Source), C.POINTER(Grid), u64, u64,
+                                                u64, i32, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -308,6 +310,17 @@ class Context:
         q, r, n = C.c_int64(), C.c_int64(), C.c_int64()
         _check(lib().smcrt_serving_stats(self.h, C.byref(q), C.byref(r), C.byref(n)), "serving_stats")
         return q.value, r.value, n.value
+
+
+def run_noalloc(wl, id_begin, npackets, seed, fluence_dev, totals_dev, precision=None, stream=None):
+    """smcrt_run_noalloc: asynchronous launch on the current device with the
+    library's fixed scratch array instead of allocated device memory.
+    fluence_dev / totals_dev are accumulated into."""
+    m = Marshalled(wl.scene, wl.source, wl.grid)
+    prec = _PREC[precision if precision is not None else wl.precision]
+    _check(lib().smcrt_run_noalloc(C.byref(m.scene), C.byref(m.source), C.byref(m.grid), int(id_begin),
+                                   int(npackets), int(seed), prec, _ptr(fluence_dev), _ptr(totals_dev), stream),
+           "run_noalloc")
 
 
 def totals_tensor(device="cuda"):

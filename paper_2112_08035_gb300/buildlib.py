@@ -30,6 +30,7 @@ UNITS = {
     "smcrt_k64.cu": ["-fmad=false"],
     "smcrt_k32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "smcrt_util.cu": [],
+    "smcrt_noalloc.cu": [],
 }
 HEADERS = ["smcrt_internal.h", "smcrt_kernel.cuh"]
 

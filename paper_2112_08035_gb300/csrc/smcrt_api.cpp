@@ -843,6 +843,14 @@ void start_scheduler(smcrt_ctx *ctx)
 
 }  // namespace
 
+namespace smcrt {
+// Field validation of scene / source / grid (no compilation, no allocation).
+int validate_scene(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid *g)
+{
+    return validate(sc, src, g);
+}
+}  // namespace smcrt
+
 extern "C" {
 
 int smcrt_version(void) { return 10000; }

@@ -113,6 +113,10 @@ cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int 
 int occupancy_fp64(int threads, int variant = 0);
 int occupancy_mixed(int threads, int variant = 0);
 cudaError_t launch_set_job(JobWork *dst, const JobWork &v, cudaStream_t stream);
+// Field validation of scene / source / grid, without compiling or
+// allocating (host runtime).
+int validate_scene(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid *g);
+
 // Round prologue: for each table entry with a deferral list, zero the
 // resume cursor of its input list and the count of its output list.
 cudaError_t launch_round_prologue(JobWork *jobs, int njobs, cudaStream_t stream);
