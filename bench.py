@@ -59,6 +59,41 @@ def three_layer_flops(t: dict) -> float:
             + t["scatters"] * FLOPS_INTERACTION)
 
 
+KERNEL_SOURCES = ["paper_2112_08035_gb300/csrc/smcrt_kernel.cuh", "paper_2112_08035_gb300/csrc/smcrt_k32.cu",
+                  "paper_2112_08035_gb300/csrc/smcrt_internal.h"]
+TRAFFIC_SUMMARY = "profiles/packets_mixed_three_layer_slab.md"
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the packet kernel from the committed ncu
+    summary, or None when the kernel source changed after that capture."""
+    path = os.path.join(ROOT, TRAFFIC_SUMMARY)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip().lstrip("-").strip()
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -217,6 +252,9 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=100)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="kernel legs only (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the timed leg (the headline is mixed)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -233,11 +271,12 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     ctx = smc.Context(local)
-    wl = W.three_layer_slab(args.packets, precision="mixed")
+    wl = W.three_layer_slab(args.packets, precision=args.precision)
     g = wl.grid
-    id0 = rank * args.packets
-    plan = ctx.plan(wl, "mixed")
-    tuned = plan.autotune(min(args.packets, 2_000_000))   # launch shape + register budget
+    from paper_2112_08035_gb300.distributed import shard_range
+    id0, _ = shard_range(rank, world, args.packets * world)   # this rank's block of ids
+    plan = ctx.plan(wl, args.precision)
+    tuned = (0, 0, -1) if args.no_autotune else plan.autotune(min(args.packets, 2_000_000))
     flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
     tot = smc.totals_tensor()
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -284,10 +323,11 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed; int64 tallies)",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64 (mixed; int64 tallies)" if args.precision == "mixed" else "f64 (int64 tallies)",
            "data": "synthetic",
            "config": {"workload": f"three_layer_slab: 3 box-SDF layers, pencil beam, {args.packets:.0e} packets "
-                                  f"per GPU, 100^3 int64 fluence grid, mixed precision",
+                                  f"per GPU, 100^3 int64 fluence grid, {args.precision} precision",
                       "packets_per_step": args.packets * world, "l2": "flushed between timed steps (256 MB write)",
                       "launch": {"blocks": tuned[0], "threads": tuned[1], "register_variant": tuned[2],
                                  "chosen_by": "smcrt_plan_autotune"}},
@@ -302,10 +342,12 @@ def main():
     flops = three_layer_flops(totals_mixed)
     achieved = flops / kernel_s / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                       "frac": achieved / peak_tflops, "traffic": None,
+                       "frac": achieved / peak_tflops, "traffic": recorded_traffic(),
+                       "traffic_note": "DRAM bytes per full-size launch from the ncu summary in profiles/ "
+                                       "(null if the kernel changed since)",
                        "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 (FMA) x {mhz:.0f} MHz "
                                      f"(median SM clock sampled under load)",
-                       "kernel": "packets_mixed",
+                       "kernel": f"packets_{args.precision}",
                        "algorithmic_flops_per_packet": flops / args.packets,
                        "atomics_per_s": totals_mixed["pieces"] / kernel_s}
     out["counters_per_packet"] = {k: totals_mixed[k] / args.packets for k in
