@@ -65,11 +65,17 @@ TRAFFIC_SUMMARY = "profiles/packets_mixed_three_layer_slab.md"
 
 
 def kernel_source_hash() -> str:
+    """sha256 of the packet kernel's sources with comments and whitespace
+    removed (a comment edit does not change the kernel)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", "", src).encode())
     return h.hexdigest()
 
 

@@ -13,7 +13,7 @@
  *     the normal from the SDF gradient, bounding box as volume of interest;
  *   - Sec. 3.1: Henyey-Greenstein scattering; absorption weighting with
  *     Russian roulette (the paper reuses its earlier codes' routines);
- *   - Sec. 3.2: fluence tallied in rectangular voxel bins.
+ *   - Sec. 3.1-3.2: fluence tallied in rectangular voxel bins.
  *
  * Units: lengths in cm, coefficients in cm^-1.  Every tally is a signed
  * 64-bit fixed-point number in units of 2^-32 packet weight (fluence: weight
@@ -125,7 +125,7 @@ typedef struct {
 } smcrt_source;
 
 /* Fluence grid: n[0] x n[1] x n[2] rectangular voxels over [lo, hi],
- * stored [z][y][x] with x fastest (Sec. 3.2 rectangular bins). */
+ * stored [z][y][x] with x fastest (Sec. 3.1-3.2 rectangular bins). */
 typedef struct {
     double lo[3];
     double hi[3];

@@ -20,7 +20,7 @@
  *     packet                                                  (Sec. 2.3),
  *   - interaction: absorption weight, Henyey-Greenstein scattering
  *     (Sec. 3.1) with Russian roulette,
- *   - track-length fluence in rectangular voxel bins          (Sec. 3.2).
+ *   - track-length fluence in rectangular voxel bins      (Sec. 3.1-3.2).
  *
  * Readings of points the paper leaves open (xi in (0,1], delta, normal
  * step, push-off, Fresnel form, roulette constants, RNG) are the ones
@@ -332,7 +332,7 @@ static void onb(const double n[3], double b1[3], double b2[3])
 }
 
 /* ------------------------------------------------------------------------
- * Track-length fluence tally (Sec. 3.2: fluence in rectangular voxels).
+ * Track-length fluence tally (Sec. 3.1-3.2: fluence grid, rectangular bins).
  * The segment p + t u, t in [0, len], is clipped to the grid box and split
  * by a 3D DDA (Amanatides & Woo, Eurographics 1987).  The parametric
  * distance to each axis' next plane is recomputed from the segment start

@@ -334,7 +334,7 @@ __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, 
 }
 
 // ---------------------------------------------------------------------------
-// Track-length tally (Sec. 3.2): 3D DDA over the grid (Amanatides & Woo
+// Track-length tally (Sec. 3.1-3.2): 3D DDA over the grid (Amanatides & Woo
 // 1987), distance to each axis' next plane recomputed from the segment
 // start; each piece adds round(w * piece * 2^32) to its voxel atomically.
 // Per-axis state lives in scalars (no dynamically indexed arrays, which

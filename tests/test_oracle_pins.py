@@ -5,7 +5,7 @@ the physics, exact invariants, or brute force on small inputs.
 Paper references: Eq. 1 (free path), Eq. 2-3 (sphere SDF), Sec. 2.2 (CSG),
 Sec. 2.3 / Fig. 2-3 (sphere tracing, Fresnel at index changes), Sec. 3.1
 (Eq. 4 scattering count, HG phase function, Table 1 penetration depth),
-Sec. 3.2 (rectangular fluence bins).
+Sec. 3.1-3.2 (rectangular fluence bins).
 """
 import math
 
@@ -315,7 +315,7 @@ def test_interface_snell_geometry_sphere():
 
 
 # --------------------------------------------------------------------------
-# Track-length tally (Sec. 3.2): DDA against brute force.
+# Track-length tally (Sec. 3.1-3.2): DDA against brute force.
 # --------------------------------------------------------------------------
 
 def test_dda_total_and_brute_force():
