@@ -95,8 +95,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB_PATH)
+            # ORACLE_LIB (tests only): load a deliberately broken build to
+            # check that the pins catch it
+            path = os.environ.get("ORACLE_LIB") or build()
+            L = C.CDLL(path)
             L.or_run.restype = C.c_int
             L.or_run.argtypes = [C.POINTER(OrScene), C.POINTER(OrSource), C.POINTER(OrGrid),
                                  C.c_uint64, C.c_uint64, C.c_uint64, C.c_void_p,

@@ -1,0 +1,62 @@
+"""Mutation tests of the oracle's pins.
+
+Each case plants one plausible mistake in a copy of the oracle source (a
+dropped term, a wrong sign or index, a transposed operand), builds it, and
+runs the pin suite against that build in a subprocess.  The pins must fail
+for every mutant: a mistake of that kind anywhere in the oracle would be
+caught.  CPU only."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "smcrt_oracle.c")
+
+# (name, exact text in the oracle, replacement)
+MUTANTS = [
+    ("philox_key_bump", "k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;", "k0 += 0x9E3779B9u; k1 += 0xBB67AE86u;"),
+    ("log_series_term", "poly = poly * z + 1.0 / 5.0;", "poly = poly * z + 1.0 / 6.0;"),
+    ("sincos_quadrant", "else if (qi == 1) { *sn = c;  *cs = -s; }", "else if (qi == 1) { *sn = c;  *cs = s; }"),
+    ("sphere_radius_sign", "return sqrt(dx * dx + dy * dy + dz * dz) - q[3];", "return sqrt(dx * dx + dy * dy + dz * dz) + q[3];"),
+    ("box_inside_term", "double inside = fmin(fmax(qx, fmax(qy, qz)), 0.0);", "double inside = fmin(fmax(qx, qy), 0.0);"),
+    ("capsule_clamp", "t = fmin(fmax(t, 0.0), 1.0);", "t = fmin(fmax(t, 0.0), 0.5);"),
+    ("subtract_sign", "if (op == 4) return fmax(a, -b);", "if (op == 4) return fmax(-a, b);"),
+    ("smooth_operands", "double h = 0.5 + 0.5 * (b - a) / k;", "double h = 0.5 + 0.5 * (a - b) / k;"),
+    ("hg_g_sign", "double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * xi);", "double t = (1.0 - g * g) / (1.0 + g + 2.0 * g * xi);"),
+    ("rotation_basis", "b2[0] = b; b2[1] = sg + n[1] * n[1] * a; b2[2] = -n[1];", "b2[0] = b; b2[1] = sg + n[0] * n[1] * a; b2[2] = -n[1];"),
+    ("fresnel_p_term", "double rp = (n1 * ct - n2 * ci) / (n1 * ct + n2 * ci);", "double rp = (n1 * ci - n2 * ct) / (n1 * ct + n2 * ci);"),
+    ("snell_eta", "double eta = n1 / n2;\n        double k = sg * (eta * ci - ct);", "double eta = n2 / n1;\n        double k = sg * (eta * ci - ct);"),
+    ("reflect_sign", "double c2 = 2.0 * c;", "double c2 = -2.0 * c;"),
+    ("dda_plane_index", "tnext[a] = ((G->lo[a] + (double)(i + 1) * dl[a]) - p[a]) / u[a];", "tnext[a] = ((G->lo[a] + (double)(i + 2) * dl[a]) - p[a]) / u[a];"),
+    ("tally_voxel_order", "size_t off = ((size_t)idx[2] * (size_t)G->n[1] + (size_t)idx[1]) * (size_t)G->n[0] + (size_t)idx[0];",
+     "size_t off = ((size_t)idx[0] * (size_t)G->n[1] + (size_t)idx[1]) * (size_t)G->n[0] + (size_t)idx[2];"),
+    ("free_path_mu", "double s = tau / mu_t;", "double s = tau / mu_s;"),
+    ("tau_consumed", "tau = tau - mu_t * L;", "tau = tau - mu_a * L;"),
+    ("absorbed_weight", "double wn = w * (mu_s / mu_t);", "double wn = w * (mu_a / mu_t);"),
+    ("roulette_gain", "P.gain += fx(w * (OR_ROULETTE_M - 1.0));", "P.gain += fx(w * OR_ROULETTE_M);"),
+    ("escape_split", "if (u[0] * src->dir[0] + u[1] * src->dir[1] + u[2] * src->dir[2] < 0.0) P.R += fx(w);",
+     "if (u[0] * src->dir[0] + u[1] * src->dir[1] + u[2] * src->dir[2] > 0.0) P.R += fx(w);"),
+    ("region_priority", "if (d < 0.0) E.region = r;", "if (d < 0.0 && E.region < 0) E.region = r;"),
+    ("disc_radius", "double rho = src->radius * sqrt(xi[0]);", "double rho = src->radius * xi[0];"),
+    ("iso_cos_theta", "double ct = 2.0 * xi[0] - 1.0;\n        double st", "double ct = xi[0];\n        double st"),
+    ("square_side", "c2 = src->radius * (2.0 * xi[1] - 1.0);", "c2 = src->radius * (2.0 * xi[0] - 1.0);"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique/found: {name}"
+    mpath = tmp_path / "mutant.c"
+    mpath.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(mpath),
+                           "-o", str(lib), "-lm"])
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"

@@ -564,3 +564,65 @@ def test_table1_penetration_depth(row):
     sel = (z > 4 * dpaper) & (z < 12 * dpaper)
     slope = np.polyfit(z[sel], np.log(phi[sel]), 1)[0]
     assert abs(-slope * dpaper - k1) < 0.08
+
+
+# --------------------------------------------------------------------------
+# Photon release (Sec. 2.1): source distributions.
+# --------------------------------------------------------------------------
+
+def _clear_scene():
+    # one tiny region far away: the packets cross only ambient medium
+    return W.Scene((W.Prim(W.SPHERE, (5.0, 5.0, 5.0, 0.1)),),
+                   (W.Region(W.prim_program([0]), 0.0, 0.0, 0.0, 1.0),), 1.0, (-6, -6, -6), (6, 6, 6))
+
+
+def _launch_histogram(src, n, R, m=48):
+    # a clear medium and a thin tally slab just below the source plane: each
+    # packet leaves track length dz in the voxel under its launch point, so
+    # the slab is a histogram of launch positions
+    dz = 0.01
+    grid = W.Grid((-R, -R, -0.2 - dz), (R, R, -0.2), (m, m, 1))
+    flu, tot, _ = _run(_clear_scene(), src, n, 41, grid=grid)
+    h = flu[0] / FX / dz
+    assert abs(h.sum() - n) < 1e-6 * n
+    c = (np.arange(m) + 0.5) / m * 2 * R - R
+    X, Y = np.meshgrid(c, c)
+    return h / n, X, Y
+
+
+def test_disc_source_uniform_over_disc():
+    R, n = 0.5, 40000
+    p, X, Y = _launch_histogram(W.Source(W.DISC, (0.0, 0.0, 0.0), (0.0, 0.0, -1.0), R), n, R)
+    r2 = float((p * (X * X + Y * Y)).sum())
+    # uniform disc: <rho^2> = R^2 / 2 (a radius drawn uniformly would give R^2 / 3)
+    assert abs(r2 - R * R / 2) < 0.02 * R * R
+    inner = float(p[X * X + Y * Y < (R / 2) ** 2].sum())
+    assert abs(inner - 0.25) < 0.02
+
+
+def test_square_source_uniform_over_square():
+    R, n = 0.4, 40000
+    p, X, Y = _launch_histogram(W.Source(W.SQUARE, (0.0, 0.0, 0.0), (0.0, 0.0, -1.0), R), n, R, m=8)
+    # 64 equal cells: each holds 1/64 of the packets (binomial 4 sigma)
+    sig = math.sqrt((1 / 64) * (63 / 64) / n)
+    assert np.all(np.abs(p - 1 / 64) < 4 * sig)
+
+
+def test_isotropic_source_directions():
+    n = 40000
+    src = W.Source(W.ISO_POINT, (0.0, 0.0, 0.0), (0.0, 0.0, -1.0))
+    # half the directions point against dir (counted as R), exactly in expectation
+    _, tot, _ = _run(_clear_scene(), src, n, 43, fluence=False)
+    assert _within(_frac(tot, "R"), 0.5, n)
+    # track-length density of a unit isotropic point source in a clear medium
+    # is 1 / (4 pi |x|^2): the expected track length in a box is its volume
+    # integral (3D midpoint quadrature of the closed form)
+    grid = W.Grid((-2.0, -2.0, 0.5), (2.0, 2.0, 0.6), (1, 1, 1))
+    flu, _, _ = _run(_clear_scene(), src, n, 44, grid=grid)
+    got = flu[0, 0, 0] / FX / n
+    mx, mz = 200, 20
+    xs = (np.arange(mx) + 0.5) / mx * 4 - 2
+    zs = 0.5 + (np.arange(mz) + 0.5) / mz * 0.1
+    X, Y, Z = np.meshgrid(xs, xs, zs, indexing="ij")
+    want = float((1.0 / (4 * math.pi * (X * X + Y * Y + Z * Z))).sum() * (4 / mx) ** 2 * (0.1 / mz))
+    assert abs(got - want) < 0.03 * want
