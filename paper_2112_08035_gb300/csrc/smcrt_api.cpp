@@ -365,6 +365,11 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     H.delta = sc->delta;
     H.ambient_n = sc->ambient_n;
     H.ambient_n32 = (float)sc->ambient_n;
+    {   // analytic normals when every region's program is short
+        int longest = 0;
+        for (int r = 0; r < nr; ++r) longest = std::max(longest, rr[r].y - rr[r].x);
+        H.analytic_nrm = longest <= kAnalyticNormalMaxInstr ? 1 : 0;
+    }
     H.delta32 = std::max((float)sc->delta, 64.f * ulp_f32(rmax));
     H.h32 = 32.f * H.delta32;
     H.max_steps = sc->max_steps;

@@ -14,7 +14,10 @@ constexpr int kMaxStack = 4;      // CSG register stack depth on the device
 constexpr int kMaxRegions = 64;
 constexpr int kMaxPrims = 4096;
 constexpr int kMaxGridSide = 1024;
-constexpr int kMaxThreads = 128;   // packet kernels are compiled for <= 128 threads per block
+constexpr int kMaxThreads = 128;
+// Longest region program (instructions) whose normal the mixed kernel takes
+// from the analytic SDF gradient; longer programs use six shared probes.
+constexpr int kAnalyticNormalMaxInstr = 4;   // packet kernels are compiled for <= 128 threads per block
 
 // Device instruction (compiled CSG program).  op: 0 push primitive;
 // 1 union, 2 smooth union, 3 intersect, 4 subtract.  prim >= 0 with a
@@ -51,6 +54,8 @@ struct DevScene {
     double delta, ambient_n;
     float delta32;            // FP32 surface threshold (>= 64 ulp of the scene extent)
     float ambient_n32;
+    int32_t analytic_nrm;     // mixed mode: normals from the analytic SDF gradient (short programs)
+    int32_t pad2;
     float h32;                // FP32 central-difference step for normals
     int64_t max_steps;
     // source

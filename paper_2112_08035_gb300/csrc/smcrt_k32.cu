@@ -233,7 +233,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         }
 
         // ---- 3. classify
-        bool move = false, fresnel = false, iter_done = false;
+        bool move = false, fresnel = false, iter_done = false, nrm_ready = false;
         bool fin = false;                      // the packet ends this iteration
         long long fin_R = 0, fin_T = 0, fin_K = 0;
         float L = 0.f;
@@ -252,8 +252,13 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                     if (E.dmin < delta) {
                         istar = E.istar;
                         dstar = E.dstar;
-                        phase = kNrm;
-                        sub = 0;
+                        if (S.analytic_nrm) {              // gradient of a short program, now
+                            grad_surface32(S, istar, px, py, pz, qx, qy, qz);
+                            nrm_ready = true;
+                        } else {                           // six probes in the next iterations
+                            phase = kNrm;
+                            sub = 0;
+                        }
                     } else {
                         L = E.dmin - 0.5f * delta;
                         move = true;
@@ -268,31 +273,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                     const int a = sub >> 1;
                     if (a == 0) qx = gg; else if (a == 1) qy = gg; else qz = gg;
                 }
-                if (++sub == 6) {
-                    const float l2 = qx * qx + qy * qy + qz * qz;
-                    bool approaching = false;
-                    if (l2 > 0.f) {
-                        const float il = rsqrtf(l2);
-                        nx = qx * il; ny = qy * il; nz = qz * il;
-                        cdot = ux * nx + uy * ny + uz * nz;
-                        approaching = (cdot > 0.f && dstar < 0.f) || (cdot < 0.f && dstar >= 0.f);
-                    }
-                    if (!approaching) {
-                        L = delta;                  // forced step along u
-                        move = true;
-                    } else if (istar < 0) {
-                        {                                          // leaves the volume: R or T
-                        const long long v = fx32(w);
-                        if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
-                        fin = true;
-                        alive = false;
-                    }
-                    } else {
-                        wadd(wa, kIntf, 1);
-                        qx = px - dstar * nx; qy = py - dstar * ny; qz = pz - dstar * nz;
-                        phase = kFar;
-                    }
-                }
+                if (++sub == 6) nrm_ready = true;
             } else if (phase == kFar) {
                 rfar = E.region;
                 phase = kNear;
@@ -306,6 +287,31 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 } else {
                     fresnel = true;
                 }
+            }
+        }
+
+        // ---- 3b. a normal is ready (analytic, or after the sixth probe)
+        if (nrm_ready) {
+            const float l2 = qx * qx + qy * qy + qz * qz;
+            bool approaching = false;
+            if (l2 > 0.f) {
+                const float il = rsqrtf(l2);
+                nx = qx * il; ny = qy * il; nz = qz * il;
+                cdot = ux * nx + uy * ny + uz * nz;
+                approaching = (cdot > 0.f && dstar < 0.f) || (cdot < 0.f && dstar >= 0.f);
+            }
+            if (!approaching) {
+                L = delta;                          // forced step along u
+                move = true;
+            } else if (istar < 0) {                 // leaves the volume: R or T
+                const long long v = fx32(w);
+                if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
+                fin = true;
+                alive = false;
+            } else {
+                wadd(wa, kIntf, 1);
+                qx = px - dstar * nx; qy = py - dstar * ny; qz = pz - dstar * nz;
+                phase = kFar;
             }
         }
 
@@ -393,7 +399,8 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             const float eta = n1 / n2;
             const float st2 = eta * eta * ((1.f - ci) * (1.f + ci));
             const int zeros = (nx == 0.f) + (ny == 0.f) + (nz == 0.f);
-            if (ci < kGrazeCos || fabsf(st2 - 1.f) < kCritBand || zeros != 2) {
+            const bool curved_noisy = !S.analytic_nrm && zeros != 2;   // probe normals on curved faces
+            if (ci < kGrazeCos || fabsf(st2 - 1.f) < kCritBand || curved_noisy) {
                 wadd(wa, kRefined, 1);
                 refine64(S, istar, rnear, rfar, sg, r.x, qx, qy, qz, ux, uy, uz, nx, ny, nz);
                 px = qx; py = qy; pz = qz;

@@ -325,6 +325,106 @@ __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float
     return E;
 }
 
+// Value and analytic gradient of one primitive (FP32).  Sphere and capsule:
+// unit vector from the nearest point of the centre / segment; box: outside,
+// the normalised positive part of q = |p - c| - h with the signs of p - c;
+// inside, the axis of the largest component of q.
+__device__ __forceinline__ float prim_grad32(const DevScene &S, int kind, int i, float x, float y, float z,
+                                             float &gx, float &gy, float &gz)
+{
+    const float4 A = __ldg(S.p32 + 2 * i);
+    if (kind == 0) {
+        const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
+        const float l = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float il = l > 0.f ? 1.f / l : 0.f;
+        gx = dx * il; gy = dy * il; gz = dz * il;
+        return l - A.w;
+    }
+    const float4 B = __ldg(S.p32 + 2 * i + 1);
+    if (kind == 1) {
+        const float px = x - A.x, py = y - A.y, pz = z - A.z;
+        const float qx = fabsf(px) - B.x, qy = fabsf(py) - B.y, qz = fabsf(pz) - B.z;
+        const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+        const float o = sqrtf(mx * mx + my * my + mz * mz);
+        if (o > 0.f) {
+            const float io = 1.f / o;
+            gx = copysignf(mx * io, px); gy = copysignf(my * io, py); gz = copysignf(mz * io, pz);
+            return o;
+        }
+        gx = gy = gz = 0.f;
+        if (qx >= qy && qx >= qz) { gx = copysignf(1.f, px); return qx; }
+        if (qy >= qz) { gy = copysignf(1.f, py); return qy; }
+        gz = copysignf(1.f, pz);
+        return qz;
+    }
+    const float pax = x - A.x, pay = y - A.y, paz = z - A.z;
+    float t = (pax * B.x + pay * B.y + paz * B.z) * B.w;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float dx = pax - B.x * t, dy = pay - B.y * t, dz = paz - B.z * t;
+    const float l = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float il = l > 0.f ? 1.f / l : 0.f;
+    gx = dx * il; gy = dy * il; gz = dz * il;
+    return l - A.w;
+}
+
+// CSG on (value, gradient) pairs: min / max / max(a, -b) select an operand's
+// gradient; for the polynomial smooth minimum d/da = h and d/db = 1 - h.
+__device__ __forceinline__ void csg_grad32(int op, float &a, float &ax, float &ay, float &az, float b, float bx,
+                                           float by, float bz, float kinv)
+{
+    if (op == 1) {
+        if (b < a) { a = b; ax = bx; ay = by; az = bz; }
+    } else if (op == 3) {
+        if (b > a) { a = b; ax = bx; ay = by; az = bz; }
+    } else if (op == 4) {
+        if (-b > a) { a = -b; ax = -bx; ay = -by; az = -bz; }
+    } else {
+        const float k = 1.0f / kinv;
+        float h = 0.5f + 0.5f * (b - a) * kinv;
+        h = fminf(fmaxf(h, 0.f), 1.f);
+        const float m = b + (a - b) * h;
+        a = m - k * h * (1.f - h);
+        ax = h * ax + (1.f - h) * bx; ay = h * ay + (1.f - h) * by; az = h * az + (1.f - h) * bz;
+    }
+}
+
+// Value and gradient of one surface's SDF (region program, or the bounding
+// box for r = -1): used for analytic normals on short programs.
+static __device__ __noinline__ float grad_surface32(const DevScene &S, int r, float x, float y, float z, float &gx,
+                                             float &gy, float &gz)
+{
+    if (r < 0) {
+        const float px = x - S.bbc32[0], py = y - S.bbc32[1], pz = z - S.bbc32[2];
+        const float qx = fabsf(px) - S.bbh32[0], qy = fabsf(py) - S.bbh32[1], qz = fabsf(pz) - S.bbh32[2];
+        gx = gy = gz = 0.f;
+        if (qx >= qy && qx >= qz) { gx = copysignf(1.f, px); return qx; }
+        if (qy >= qz) { gy = copysignf(1.f, py); return qy; }
+        gz = copysignf(1.f, pz);
+        return qz;
+    }
+    const int2 rr = __ldg(S.rrange + r);
+    float v[kMaxStack], vx[kMaxStack], vy[kMaxStack], vz[kMaxStack];
+    int sp = 0;
+    for (int i = rr.x; i < rr.y; ++i) {
+        const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
+        const int op = ins.x & 0xff, kind = ins.x >> 8;
+        float a = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+        if (ins.y >= 0) a = prim_grad32(S, kind, ins.y, x, y, z, ax, ay, az);
+        if (op == 0) {
+            v[sp] = a; vx[sp] = ax; vy[sp] = ay; vz[sp] = az;
+            ++sp;
+        } else if (ins.y >= 0) {
+            csg_grad32(op, v[sp - 1], vx[sp - 1], vy[sp - 1], vz[sp - 1], a, ax, ay, az, __int_as_float(ins.w));
+        } else {
+            --sp;
+            csg_grad32(op, v[sp - 1], vx[sp - 1], vy[sp - 1], vz[sp - 1], v[sp], vx[sp], vy[sp], vz[sp],
+                       __int_as_float(ins.w));
+        }
+    }
+    gx = vx[0]; gy = vy[0]; gz = vz[0];
+    return v[0];
+}
+
 // SDF of one surface in FP64 (region program, or the bounding box for -1).
 __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, double y, double z)
 {

@@ -201,6 +201,11 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     H.delta = sc->delta;
     H.ambient_n = sc->ambient_n;
     H.ambient_n32 = (float)sc->ambient_n;
+    {
+        int longest = 0;
+        for (int r = 0; r < nr; ++r) longest = (rr[r].y - rr[r].x) > longest ? (rr[r].y - rr[r].x) : longest;
+        H.analytic_nrm = longest <= kAnalyticNormalMaxInstr ? 1 : 0;
+    }
     H.delta32 = std::fmax((float)sc->delta, 64.f * ulp32(rmax));
     H.h32 = 32.f * H.delta32;
     H.max_steps = sc->max_steps;
