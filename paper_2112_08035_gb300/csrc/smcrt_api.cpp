@@ -262,6 +262,115 @@ uint64_t shape_key(const smcrt_scene *sc, int precision, const smcrt_grid *g)
     return h;
 }
 
+// A region whose program is a left fold of one operator (union or smooth
+// union, one k) over primitives: returns the primitives in fold order.
+bool fold_region(const smcrt_scene *sc, int r, int *op, double *k, std::vector<int> *prims)
+{
+    const smcrt_region &R = sc->regions[r];
+    const smcrt_csg_node *nd = sc->nodes + R.node_begin;
+    if (R.node_count < 3 || (R.node_count - 1) % 2 != 0 || nd[0].op != SMCRT_OP_PRIM) return false;
+    prims->clear();
+    prims->push_back(nd[0].prim);
+    int o = -1;
+    double kk = 0.0;
+    for (int i = 1; i + 1 < R.node_count; i += 2) {
+        const int bop = nd[i + 1].op;
+        if (nd[i].op != SMCRT_OP_PRIM || (bop != SMCRT_OP_UNION && bop != SMCRT_OP_SMOOTH_UNION)) return false;
+        if (o < 0) {
+            o = bop;
+            kk = bop == SMCRT_OP_SMOOTH_UNION ? nd[i + 1].k : 0.0;
+        } else if (bop != o || (bop == SMCRT_OP_SMOOTH_UNION && nd[i + 1].k != kk)) {
+            return false;
+        }
+        prims->push_back(nd[i].prim);
+    }
+    *op = o;
+    *k = kk;
+    return true;
+}
+
+struct CullGrid {
+    int region = -1, g = 0, op = 0;
+    float lo[3] = {0, 0, 0}, inv_s[3] = {0, 0, 0}, rmax = 0, kinv = 0;
+    std::vector<int32_t> off, list;
+};
+
+// Uniform grid over the longest fold region (>= kCullMinPrims primitives):
+// each cell lists the primitives whose bounding box lies within R' of the
+// cell (R' = 1.05 R plus 1% of a cell, covering FP32 cell-index rounding);
+// the grid extends R beyond every primitive, so outside it and for unlisted
+// primitives the region's distance exceeds R; the kernel bounds the value
+// by R (union) or R - k/4 (smooth union, which lies at most k/4 below min).
+void build_cull(const smcrt_scene *sc, CullGrid &cg)
+{
+    int best = -1, bop = 0;
+    double bk = 0.0;
+    std::vector<int> prims, bprims;
+    for (int r = 0; r < sc->nregions; ++r) {
+        int op;
+        double k;
+        if (fold_region(sc, r, &op, &k, &prims) && (int)prims.size() >= kCullMinPrims &&
+            (best < 0 || prims.size() > bprims.size())) {
+            best = r; bop = op; bk = k; bprims = prims;
+        }
+    }
+    if (best < 0) return;
+    const int n = (int)bprims.size();
+    std::vector<double> plo(3 * n), phi(3 * n);
+    double blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int j = 0; j < n; ++j) {
+        const smcrt_prim &P = sc->prims[bprims[j]];
+        for (int a = 0; a < 3; ++a) {
+            double lo, hi;
+            if (P.kind == SMCRT_SPHERE) { lo = P.p[a] - P.p[3]; hi = P.p[a] + P.p[3]; }
+            else if (P.kind == SMCRT_BOX) { lo = P.p[a] - P.p[3 + a]; hi = P.p[a] + P.p[3 + a]; }
+            else {
+                lo = std::min(P.p[a], P.p[3 + a]) - P.p[6];
+                hi = std::max(P.p[a], P.p[3 + a]) + P.p[6];
+            }
+            plo[3 * j + a] = lo; phi[3 * j + a] = hi;
+            blo[a] = std::min(blo[a], lo); bhi[a] = std::max(bhi[a], hi);
+        }
+    }
+    const int G = kCullGrid;
+    const double ext = std::max(bhi[0] - blo[0], std::max(bhi[1] - blo[1], bhi[2] - blo[2]));
+    const double R = std::max(ext / G, bop == SMCRT_OP_SMOOTH_UNION ? 4.0 * bk : 0.0);
+    double glo[3], s[3];
+    for (int a = 0; a < 3; ++a) {
+        glo[a] = blo[a] - R;
+        s[a] = (bhi[a] + R - glo[a]) / G;
+    }
+    const double smax = std::max(s[0], std::max(s[1], s[2]));
+    const double Rl = 1.05 * std::max(R, smax) + 0.01 * smax;
+    cg.off.assign((size_t)G * G * G + 1, 0);
+    cg.list.clear();
+    for (int cz = 0; cz < G; ++cz)
+        for (int cy = 0; cy < G; ++cy)
+            for (int cx = 0; cx < G; ++cx) {
+                const int c = (cz * G + cy) * G + cx;
+                const double clo[3] = {glo[0] + cx * s[0], glo[1] + cy * s[1], glo[2] + cz * s[2]};
+                cg.off[c] = (int32_t)cg.list.size();
+                for (int j = 0; j < n; ++j) {
+                    double d2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        const double gap = std::max(0.0, std::max(clo[a] - phi[3 * j + a], plo[3 * j + a] - (clo[a] + s[a])));
+                        d2 += gap * gap;
+                    }
+                    if (d2 <= Rl * Rl) cg.list.push_back(bprims[j]);
+                }
+            }
+    cg.off[(size_t)G * G * G] = (int32_t)cg.list.size();
+    cg.region = best;
+    cg.g = G;
+    cg.op = bop;
+    cg.kinv = bop == SMCRT_OP_SMOOTH_UNION ? (float)(1.0 / bk) : 0.f;
+    cg.rmax = (float)(bop == SMCRT_OP_SMOOTH_UNION ? R - 0.25 * bk : R);
+    for (int a = 0; a < 3; ++a) {
+        cg.lo[a] = (float)glo[a];
+        cg.inv_s[a] = (float)(1.0 / s[a]);
+    }
+}
+
 // Validate, compile and upload a plan.  With a stream (the serving
 // scheduler) the scene buffer is allocated and filled stream-ordered, no
 // device-wide synchronisation happens, and no launch ring is created.
@@ -325,6 +434,10 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     const size_t o_rr = take(sizeof(int2) * nr);
     const size_t o_r64 = take(sizeof(double) * 8 * nr);
     const size_t o_r32 = take(sizeof(float4) * 2 * nr);
+    CullGrid cg;
+    if (precision == SMCRT_MIXED) build_cull(sc, cg);
+    const size_t o_coff = take(sizeof(int32_t) * cg.off.size());
+    const size_t o_clist = take(sizeof(int32_t) * cg.list.size());
     const size_t total = off;
 
     std::unique_ptr<smcrt_plan> pl(new smcrt_plan());
@@ -365,6 +478,17 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     H.delta = sc->delta;
     H.ambient_n = sc->ambient_n;
     H.ambient_n32 = (float)sc->ambient_n;
+    H.cull_region = cg.region;
+    H.cull_g = cg.g;
+    H.cull_op = cg.op;
+    for (int a = 0; a < 3; ++a) {
+        H.cull_lo[a] = cg.lo[a];
+        H.cull_inv_s[a] = cg.inv_s[a];
+    }
+    H.cull_rmax = cg.rmax;
+    H.cull_kinv = cg.kinv;
+    H.cull_off = cg.region >= 0 ? (const int32_t *)(base + o_coff) : nullptr;
+    H.cull_list = cg.region >= 0 ? (const int32_t *)(base + o_clist) : nullptr;
     {   // analytic normals when every region's program is short
         int longest = 0;
         for (int r = 0; r < nr; ++r) longest = std::max(longest, rr[r].y - rr[r].x);
@@ -404,6 +528,8 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     std::memcpy(hb.data() + o_rr, rr.data(), sizeof(int2) * nr);
     std::memcpy(hb.data() + o_r64, reg64.data(), sizeof(double) * 8 * nr);
     std::memcpy(hb.data() + o_r32, reg32.data(), sizeof(float4) * 2 * nr);
+    if (!cg.off.empty()) std::memcpy(hb.data() + o_coff, cg.off.data(), sizeof(int32_t) * cg.off.size());
+    if (!cg.list.empty()) std::memcpy(hb.data() + o_clist, cg.list.data(), sizeof(int32_t) * cg.list.size());
     pl->dscene = (DevScene *)(base + o_scene);
     pl->cells = (size_t)g->n[0] * g->n[1] * g->n[2];
     if (serving_stream) {

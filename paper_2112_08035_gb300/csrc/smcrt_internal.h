@@ -17,7 +17,10 @@ constexpr int kMaxGridSide = 1024;
 constexpr int kMaxThreads = 128;
 // Longest region program (instructions) whose normal the mixed kernel takes
 // from the analytic SDF gradient; longer programs use six shared probes.
-constexpr int kAnalyticNormalMaxInstr = 4;   // packet kernels are compiled for <= 128 threads per block
+constexpr int kAnalyticNormalMaxInstr = 4;
+// Fold regions with at least this many primitives get a culling grid.
+constexpr int kCullMinPrims = 16;
+constexpr int kCullGrid = 16;   // packet kernels are compiled for <= 128 threads per block
 
 // Device instruction (compiled CSG program).  op: 0 push primitive;
 // 1 union, 2 smooth union, 3 intersect, 4 subtract.  prim >= 0 with a
@@ -55,7 +58,17 @@ struct DevScene {
     float delta32;            // FP32 surface threshold (>= 64 ulp of the scene extent)
     float ambient_n32;
     int32_t analytic_nrm;     // mixed mode: normals from the analytic SDF gradient (short programs)
-    int32_t pad2;
+    // Spatial culling of one long fold region (mixed mode only): a G^3 grid
+    // of cells, each listing the region's primitives within distance R of
+    // the cell; elsewhere the region's value is bounded by R - k/4.
+    int32_t cull_region;      // -1: none
+    int32_t cull_g;
+    int32_t cull_op;          // 1 union, 2 smooth union
+    float cull_lo[3], cull_inv_s[3];
+    float cull_rmax;          // R (union) or R - k/4 (smooth union)
+    float cull_kinv;
+    const int32_t *cull_off;  // G^3 + 1 prefix offsets into cull_list
+    const int32_t *cull_list; // primitive indices, in the region's fold order
     float h32;                // FP32 central-difference step for normals
     int64_t max_steps;
     // source

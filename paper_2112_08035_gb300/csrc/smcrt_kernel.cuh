@@ -312,12 +312,50 @@ __device__ __forceinline__ Eval64 scene_eval64(const DevScene &S, double x, doub
     return E;
 }
 
+// Value of the culled fold region at p: the fold over the primitives listed
+// for p's cell, bounded by cull_rmax (every unlisted primitive is farther
+// than R from the cell, so it cannot change the value below that bound).
+__device__ __forceinline__ float culled_region32(const DevScene &S, float x, float y, float z)
+{
+    const int g = S.cull_g;
+    const int cx = __float2int_rd((x - S.cull_lo[0]) * S.cull_inv_s[0]);
+    const int cy = __float2int_rd((y - S.cull_lo[1]) * S.cull_inv_s[1]);
+    const int cz = __float2int_rd((z - S.cull_lo[2]) * S.cull_inv_s[2]);
+    if ((unsigned)cx >= (unsigned)g || (unsigned)cy >= (unsigned)g || (unsigned)cz >= (unsigned)g)
+        return S.cull_rmax;
+    const int c = (cz * g + cy) * g + cx;
+    const int o0 = __ldg(S.cull_off + c), o1 = __ldg(S.cull_off + c + 1);
+    if (o1 <= o0) return S.cull_rmax;
+    int i = __ldg(S.cull_list + o0);
+    float acc = prim32(S, __ldg(S.pkind + i), i, x, y, z);
+    for (int j = o0 + 1; j < o1; ++j) {
+        i = __ldg(S.cull_list + j);
+        acc = csg32(S.cull_op, acc, prim32(S, __ldg(S.pkind + i), i, x, y, z), S.cull_kinv);
+    }
+    return fminf(acc, S.cull_rmax);
+}
+
+__device__ __forceinline__ void region_end32(Eval32 *E, int r, float d, int sel)
+{
+    if (d < 0.f) E->region = r;
+    const float ad = fabsf(d);
+    if (ad < E->dmin) { E->dmin = ad; E->istar = r; E->dstar = d; }
+    if (r == sel) E->dsel = d;
+}
+
 __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float y, float z, int sel)
 {
     Eval32 E;
     E.dmin = __int_as_float(0x7f800000);
     E.dstar = 0.f; E.dsel = 0.f; E.istar = -1; E.region = -1;
-    run_prog32<true>(S, 0, S.ninstr, x, y, z, sel, &E);
+    if (S.cull_region < 0) {
+        run_prog32<true>(S, 0, S.ninstr, x, y, z, sel, &E);
+    } else {   // regions in index order: before, the culled one, after
+        const int2 rr = __ldg(S.rrange + S.cull_region);
+        run_prog32<true>(S, 0, rr.x, x, y, z, sel, &E);
+        region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel);
+        run_prog32<true>(S, rr.y, S.ninstr, x, y, z, sel, &E);
+    }
     const float db = box32(x, y, z, S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2]);
     E.dbox = db;
     if (fabsf(db) < E.dmin) { E.dmin = fabsf(db); E.istar = -1; E.dstar = db; }

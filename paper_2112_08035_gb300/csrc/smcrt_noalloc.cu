@@ -201,6 +201,7 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     H.delta = sc->delta;
     H.ambient_n = sc->ambient_n;
     H.ambient_n32 = (float)sc->ambient_n;
+    H.cull_region = -1;   // no culling grid in the fixed scratch
     {
         int longest = 0;
         for (int r = 0; r < nr; ++r) longest = (rr[r].y - rr[r].x) > longest ? (rr[r].y - rr[r].x) : longest;
