@@ -51,7 +51,8 @@ class OrScene(C.Structure):
                 ("nodes", C.POINTER(OrNode)), ("nnodes", C.c_int32),
                 ("regions", C.POINTER(OrRegion)), ("nregions", C.c_int32),
                 ("ambient_n", C.c_double), ("bbox_lo", C.c_double * 3),
-                ("bbox_hi", C.c_double * 3), ("delta", C.c_double), ("max_steps", C.c_int64)]
+                ("bbox_hi", C.c_double * 3), ("delta", C.c_double), ("max_steps", C.c_int64),
+                ("stepping", C.c_int32), ("pad", C.c_int32)]
 
 
 class OrSource(C.Structure):
@@ -78,6 +79,7 @@ PACKET_DTYPE = np.dtype([(f, np.int64) for f in PACKET_FIELDS])
 _PRIM_KIND = {W.SPHERE: 0, W.BOX: 1, W.CAPSULE: 2}
 _OP = {W.PRIM: 0, W.UNION: 1, W.SMOOTH_UNION: 2, W.INTERSECT: 3, W.SUBTRACT: 4}
 _SRC_KIND = {W.PENCIL: 0, W.DISC: 1, W.SQUARE: 2, W.ISO_POINT: 3}
+_STEPPING = {W.SPHERE_TRACING: 0, W.SEGMENT: 1}
 
 
 def build(force: bool = False) -> str:
@@ -124,6 +126,8 @@ def lib():
                                         C.POINTER(C.c_double), C.POINTER(C.c_int),
                                         C.POINTER(C.c_int), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]
+            L.or_segment_step.restype = C.c_double
+            L.or_segment_step.argtypes = [C.POINTER(OrScene), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_region_sdf.restype = C.c_double
             L.or_region_sdf.argtypes = [C.POINTER(OrScene), C.c_int, C.POINTER(C.c_double)]
             L.or_surface_normal.restype = C.c_int
@@ -164,7 +168,8 @@ class _SceneHolder:
         self.prims, self.nodes, self.regs = prims, nodes, regs
         self.s = OrScene(prims, len(scene.prims), nodes, len(nodes_l), regs, len(scene.regions),
                          float(scene.ambient_n), (C.c_double * 3)(*scene.bbox_lo),
-                         (C.c_double * 3)(*scene.bbox_hi), float(scene.delta), int(scene.max_steps))
+                         (C.c_double * 3)(*scene.bbox_hi), float(scene.delta), int(scene.max_steps),
+                         _STEPPING[scene.stepping], 0)
 
 
 def _source(src: W.Source) -> OrSource:
@@ -294,6 +299,12 @@ def scene_eval(scene: W.Scene, p):
                         C.byref(region), C.byref(dbox), C.byref(dstar))
     return dict(dmin=dmin.value, istar=istar.value, region=region.value, dbox=dbox.value,
                 dstar=dstar.value)
+
+
+def segment_step(scene: W.Scene, p, u) -> float:
+    """The segment-stepping move from p along u (0 within delta of a surface)."""
+    sh = _SceneHolder(scene)
+    return lib().or_segment_step(C.byref(sh.s), (C.c_double * 3)(*p), (C.c_double * 3)(*u))
 
 
 def region_sdf(scene: W.Scene, r: int, p) -> float:

@@ -55,6 +55,8 @@ typedef struct {
     double bbox_lo[3], bbox_hi[3];
     double delta;
     int64_t max_steps;
+    int32_t stepping;          /* 0 sphere tracing (Sec. 2.3), 1 segment stepping (below) */
+    int32_t pad;
 } or_scene;
 typedef struct { int32_t kind; int32_t pad; double pos[3], dir[3], radius; } or_source; /* 0 pencil,1 disc,2 square,3 iso */
 typedef struct { double lo[3], hi[3]; int32_t n[3]; int32_t pad; } or_grid;
@@ -259,17 +261,29 @@ static double bbox_sdf(const or_scene *S, const double p[3])
  * box.  region = highest-index region whose SDF is negative (-1 ambient);
  * d_min = min |d| over regions, then the bounding box; istar is the
  * surface attaining it (lowest region index on ties, box = -1 last). */
-typedef struct { double dmin; double dstar; int istar; int region; double dbox; } or_eval;
+typedef struct { double dmin; double dstar; int istar; int region; double dbox; double dsoft; } or_eval;
+
+/* 1 if region r's program contains a smooth union (its boundary is then not
+ * made of primitive boundaries). */
+static int region_soft(const or_scene *S, int r)
+{
+    const or_region *R = &S->regions[r];
+    for (int i = 0; i < R->count; ++i)
+        if (S->nodes[R->begin + i].op == 2) return 1;
+    return 0;
+}
 
 static or_eval scene_eval(const or_scene *S, const double p[3], or_totals *T)
 {
     or_eval E;
     E.dmin = INFINITY; E.dstar = 0.0; E.istar = -1; E.region = -1;
+    E.dsoft = INFINITY;      /* min |d| over regions with a smooth union */
     for (int r = 0; r < S->nregions; ++r) {
         double d = region_sdf(S, r, p, T);
         if (d < 0.0) E.region = r;
         double ad = fabs(d);
         if (ad < E.dmin) { E.dmin = ad; E.istar = r; E.dstar = d; }
+        if (region_soft(S, r) && ad < E.dsoft) E.dsoft = ad;
     }
     E.dbox = bbox_sdf(S, p);
     if (fabs(E.dbox) < E.dmin) { E.dmin = fabs(E.dbox); E.istar = -1; E.dstar = E.dbox; }
@@ -537,6 +551,93 @@ static void launch(const or_source *src, double p[3], double u[3], double *tau, 
     *tau = -or_log(xi[3]);
 }
 
+/* ------------------------------------------------------------------------
+ * Segment stepping (scene option; Sec. 5 names segment tracing, which
+ * lengthens sphere-tracing steps with bounds taken along the ray, as the
+ * remedy for the many small steps of packets travelling nearly parallel to
+ * a surface).  Sphere tracing moves by d_min, a bound valid in every
+ * direction.  Along the packet's own direction u a longer move is safe:
+ *   - sphere, box: t = distance along the ray to the surface offset by
+ *     delta/2 (grown when p is outside, shrunk when inside).  On [0, t) the
+ *     primitive's |SDF| stays above delta/2, so its sign cannot change;
+ *   - a region built by hard CSG (union = min, intersection = max,
+ *     subtraction = max(a, -b)) changes sign only where one of its
+ *     primitives does, so the minimum of t over its primitives bounds it;
+ *   - regions with a smooth union, and capsules: the isotropic |d| - delta/2;
+ *   - the bounding box: its exit distance, shrunk by delta/2.
+ * The step is max(d_min - delta/2, minimum of the bounds): never shorter
+ * than plain sphere tracing.  It ends delta/2 short of the first surface,
+ * where the next evaluation finds d_min < delta and the interface routine
+ * of Sec. 2.3 runs unchanged.
+ * ---------------------------------------------------------------------- */
+static double segment_sphere(const double *q, double d, const double p[3], const double u[3], double dh)
+{
+    double rr = d > 0.0 ? q[3] + dh : q[3] - dh;
+    double ox = p[0] - q[0], oy = p[1] - q[1], oz = p[2] - q[2];
+    double b = ox * u[0] + oy * u[1] + oz * u[2];
+    double cc = ox * ox + oy * oy + oz * oz - rr * rr;
+    double disc = b * b - cc;
+    double t;
+    if (d > 0.0) {                       /* outside: entry of the grown sphere */
+        if (b >= 0.0 || disc < 0.0) return INFINITY;
+        t = cc / (sqrt(disc) - b);       /* near root, free of cancellation */
+    } else {                             /* inside: exit of the shrunk sphere */
+        if (disc < 0.0) return 0.0;
+        if (b > 0.0) t = -cc / (b + sqrt(disc));
+        else t = sqrt(disc) - b;
+    }
+    return t > 0.0 ? t : 0.0;
+}
+
+static double segment_box(const double c[3], const double h[3], double d, const double p[3],
+                          const double u[3], double dh)
+{
+    double e = d > 0.0 ? dh : -dh;
+    double tn = -INFINITY, tf = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double lo = c[a] - (h[a] + e), hi = c[a] + (h[a] + e);
+        if (u[a] != 0.0) {
+            double t0 = (lo - p[a]) / u[a], t1 = (hi - p[a]) / u[a];
+            tn = fmax(tn, fmin(t0, t1));
+            tf = fmin(tf, fmax(t0, t1));
+        } else if (p[a] < lo || p[a] > hi) {
+            return d > 0.0 ? INFINITY : 0.0;
+        }
+    }
+    if (d > 0.0) {                       /* outside: entry of the grown box */
+        if (tn > tf || tf < 0.0) return INFINITY;
+        return tn > 0.0 ? tn : 0.0;
+    }
+    return tf > 0.0 ? tf : 0.0;          /* inside: exit of the shrunk box */
+}
+
+static double segment_prim(const or_prim *pr, const double p[3], const double u[3], double dh)
+{
+    double d = sdf_prim(pr, p);
+    if (!(fabs(d) > dh)) return 0.0;
+    if (pr->kind == 0) return segment_sphere(pr->p, d, p, u, dh);
+    if (pr->kind == 1) return segment_box(pr->p, pr->p + 3, d, p, u, dh);
+    return fabs(d) - dh;                 /* capsule: isotropic bound */
+}
+
+/* Largest safe move from p along u (scene evaluated at p in E). */
+static double segment_bound(const or_scene *S, const or_eval *E, const double p[3], const double u[3])
+{
+    double dh = 0.5 * S->delta;
+    double t = E->dsoft - dh;
+    for (int r = 0; r < S->nregions; ++r) {
+        if (region_soft(S, r)) continue;
+        const or_region *R = &S->regions[r];
+        for (int i = 0; i < R->count; ++i) {
+            const or_node *nd = &S->nodes[R->begin + i];
+            if (nd->op == 0) t = fmin(t, segment_prim(&S->prims[nd->prim], p, u, dh));
+        }
+    }
+    double c[3], h[3];
+    bbox_center_half(S, c, h);
+    return fmin(t, segment_box(c, h, E->dbox, p, u, dh));
+}
+
 #define OR_W_ROULETTE 1e-4
 #define OR_ROULETTE_M 10.0
 
@@ -564,6 +665,7 @@ static void run_packet(const or_scene *S, const or_source *src, const or_grid *G
             L = S->delta;                      /* not approaching: forced step */
         } else {
             L = E.dmin - 0.5 * S->delta;       /* stop short: never cross by rounding */
+            if (S->stepping == 1) L = fmax(L, segment_bound(S, &E, p, u));
         }
         {
             double mu_a = 0.0, mu_s = 0.0, g = 0.0;
@@ -630,7 +732,7 @@ int or_run(const or_scene *S, const or_source *src, const or_grid *G, uint64_t i
            uint64_t id_end, uint64_t seed, int64_t *flu, or_totals *tot, or_packet *rec)
 {
     if (!S || !src || !G || !tot) return -1;
-    if (!(S->delta > 0.0) || S->nregions < 0) return -2;
+    if (!(S->delta > 0.0) || S->nregions < 0 || S->stepping < 0 || S->stepping > 1) return -2;
     for (int r = 0; r < S->nregions; ++r) {     /* postfix stack check */
         int sp = 0;
         const or_region *R = &S->regions[r];
@@ -660,6 +762,15 @@ void or_scene_eval(const or_scene *S, const double p[3], double *dmin, int *ista
     memset(&T, 0, sizeof T);
     or_eval E = scene_eval(S, p, &T);
     *dmin = E.dmin; *istar = E.istar; *region = E.region; *dbox = E.dbox; *dstar = E.dstar;
+}
+
+/* The segment-stepping move from p along u (for tests); 0 if p is within
+ * delta of a surface (no tracing step is taken there). */
+double or_segment_step(const or_scene *S, const double p[3], const double u[3])
+{
+    or_eval E = scene_eval(S, p, NULL);
+    if (!(E.dmin >= S->delta)) return 0.0;
+    return fmax(E.dmin - 0.5 * S->delta, segment_bound(S, &E, p, u));
 }
 
 double or_region_sdf(const or_scene *S, int r, const double p[3])

@@ -42,6 +42,11 @@ MUTANTS = [
     ("disc_radius", "double rho = src->radius * sqrt(xi[0]);", "double rho = src->radius * xi[0];"),
     ("iso_cos_theta", "double ct = 2.0 * xi[0] - 1.0;\n        double st", "double ct = xi[0];\n        double st"),
     ("square_side", "c2 = src->radius * (2.0 * xi[1] - 1.0);", "c2 = src->radius * (2.0 * xi[0] - 1.0);"),
+    ("segment_box_margin", "double e = d > 0.0 ? dh : -dh;", "double e = d > 0.0 ? 0.0 : -dh;"),
+    ("segment_sphere_root", "t = cc / (sqrt(disc) - b);", "t = sqrt(disc) - b;"),
+    ("segment_soft_bound", "if (region_soft(S, r) && ad < E.dsoft) E.dsoft = ad;", "if (0 && ad < E.dsoft) E.dsoft = ad;"),
+    ("segment_step_rule", "if (S->stepping == 1) L = fmax(L, segment_bound(S, &E, p, u));",
+     "if (S->stepping == 1) L = fmin(L, segment_bound(S, &E, p, u));"),
 ]
 
 

@@ -25,6 +25,9 @@ PRIM, UNION, SMOOTH_UNION, INTERSECT, SUBTRACT = (
     "prim", "union", "smooth_union", "intersect", "subtract")
 # Source kinds (photon release, Sec. 2.1 and the experiments of Sec. 3-4).
 PENCIL, DISC, SQUARE, ISO_POINT = "pencil", "disc", "square", "iso"
+# Step rules: plain sphere tracing (Sec. 2.3), or segment stepping (longer
+# steps bounded along the ray; Sec. 5 names segment tracing).
+SPHERE_TRACING, SEGMENT = "sphere_tracing", "segment"
 
 
 @dataclass(frozen=True)
@@ -61,6 +64,7 @@ class Scene:
     bbox_hi: Tuple[float, float, float]
     delta: float = 1e-6
     max_steps: int = 100_000
+    stepping: str = SPHERE_TRACING
 
 
 @dataclass(frozen=True)
@@ -98,6 +102,11 @@ class Workload:
 
     def with_packets(self, n: int) -> "Workload":
         return replace(self, npackets=int(n))
+
+    def with_stepping(self, stepping: str) -> "Workload":
+        if stepping not in (SPHERE_TRACING, SEGMENT):
+            raise ValueError(stepping)
+        return replace(self, scene=replace(self.scene, stepping=stepping))
 
 
 def prim_program(indices: Sequence[int], op: str = UNION, k: float = 0.0) -> Tuple[Node, ...]:
