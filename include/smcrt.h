@@ -95,6 +95,23 @@ typedef struct {
     double n;           /* refractive index, >= 1 */
 } smcrt_region;
 
+/* How a packet's move between scene evaluations is bounded. */
+enum smcrt_stepping {
+    /* Sphere tracing (Sec. 2.3, Fig. 3): move d_min - delta/2, the distance
+     * to the nearest surface less half the threshold. */
+    SMCRT_STEP_SPHERE_TRACING = 0,
+    /* Segment stepping (Sec. 5 names segment tracing for packets moving
+     * nearly parallel to a surface): move max(d_min - delta/2, B), where B
+     * bounds the move along the packet's own direction -- for every box
+     * and sphere of a region built by hard CSG (union, intersection,
+     * subtraction), the distance along the ray to its surface offset by
+     * delta/2; for regions with a smooth union and for capsules |d| -
+     * delta/2; for the bounding box its exit distance less delta/2.  The
+     * move stops delta/2 short of the first surface it would reach, and the
+     * interface handling is unchanged.  Same transport, fewer steps. */
+    SMCRT_STEP_SEGMENT = 1
+};
+
 typedef struct {
     const smcrt_prim *prims;       /* host array of nprims */
     int32_t nprims;                /* 1 .. 4096 */
@@ -107,6 +124,8 @@ typedef struct {
     double bbox_hi[3];             /* leaving it terminates a packet (Sec. 2.3) */
     double delta;                  /* surface threshold delta (cm), > 0 */
     int64_t max_steps;             /* per-packet step cap (grazing guard), > 0 */
+    int32_t stepping;              /* enum smcrt_stepping */
+    int32_t reserved;              /* must be 0 */
 } smcrt_scene;
 
 enum smcrt_source_kind {
@@ -268,7 +287,12 @@ int smcrt_plan_autotune(smcrt_plan *plan, uint64_t trial_packets, int32_t *block
  * Arguments as smcrt_plan_launch: packets [id_begin, id_begin + npackets)
  * with key `seed`; fluence_dev (may be NULL) and totals_dev are device
  * pointers the results are ACCUMULATED into (zero them first).  Results are
- * identical to a plan launch of the same scene, ids and seed. */
+ * identical to a plan launch of the same scene, ids and seed, except in
+ * MIXED precision for scenes with a union or smooth-union region of 16 or
+ * more primitives: a plan evaluates that region through a spatial cell list
+ * (a different, equally valid distance bound away from the surface), this
+ * call evaluates it in full, so the two agree statistically, not bit for
+ * bit. */
 int smcrt_run_noalloc(const smcrt_scene *scene, const smcrt_source *source, const smcrt_grid *grid,
                       uint64_t id_begin, uint64_t npackets, uint64_t seed, int32_t precision,
                       int64_t *fluence_dev, smcrt_totals *totals_dev, void *stream);

@@ -30,6 +30,7 @@ FX = 2.0 ** 32
 _PRIM_KIND = {"sphere": 0, "box": 1, "capsule": 2}
 _OP = {"prim": 0, "union": 1, "smooth_union": 2, "intersect": 3, "subtract": 4}
 _SRC_KIND = {"pencil": 0, "disc": 1, "square": 2, "iso": 3}
+_STEPPING = {"sphere_tracing": 0, "segment": 1}
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
 
@@ -51,7 +52,8 @@ class Scene(C.Structure):
                 ("nodes", C.POINTER(CsgNode)), ("nnodes", C.c_int32),
                 ("regions", C.POINTER(Region)), ("nregions", C.c_int32),
                 ("ambient_n", C.c_double), ("bbox_lo", C.c_double * 3), ("bbox_hi", C.c_double * 3),
-                ("delta", C.c_double), ("max_steps", C.c_int64)]
+                ("delta", C.c_double), ("max_steps", C.c_int64), ("stepping", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Source(C.Structure):
@@ -167,7 +169,8 @@ class Marshalled:
         self.regions = regs
         self.scene = Scene(self.prims, np_, self.nodes, len(nodes), regs, len(scene.regions),
                            float(scene.ambient_n), (C.c_double * 3)(*scene.bbox_lo),
-                           (C.c_double * 3)(*scene.bbox_hi), float(scene.delta), int(scene.max_steps))
+                           (C.c_double * 3)(*scene.bbox_hi), float(scene.delta), int(scene.max_steps),
+                           _STEPPING[scene.stepping], 0)
         self.source = Source(_SRC_KIND[source.kind], 0, (C.c_double * 3)(*source.pos),
                              (C.c_double * 3)(*source.dir), float(source.radius))
         self.grid = Grid((C.c_double * 3)(*grid.lo), (C.c_double * 3)(*grid.hi),

@@ -99,6 +99,7 @@ int validate(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid *g
             return SMCRT_ERR_BAD_SCENE;
     if (!(sc->delta > 0 && finite(sc->delta))) return SMCRT_ERR_BAD_SCENE;
     if (sc->max_steps < 1 || sc->max_steps > (int64_t(1) << 31)) return SMCRT_ERR_BAD_SCENE;
+    if (sc->stepping != SMCRT_STEP_SPHERE_TRACING && sc->stepping != SMCRT_STEP_SEGMENT) return SMCRT_ERR_BAD_SCENE;
     if (src->kind < SMCRT_SRC_PENCIL || src->kind > SMCRT_SRC_ISO_POINT) return SMCRT_ERR_BAD_SCENE;
     const double dl = std::sqrt(src->dir[0] * src->dir[0] + src->dir[1] * src->dir[1] + src->dir[2] * src->dir[2]);
     if (!(std::fabs(dl - 1.0) < 1e-9)) return SMCRT_ERR_BAD_SCENE;
@@ -168,6 +169,7 @@ int compile(const smcrt_scene *sc, std::vector<Instr> &ins, std::vector<double> 
         }
         if (depth != 1) return SMCRT_ERR_BAD_SCENE;
         ins.back().region = r;
+        if (region_is_soft(sc, r)) ins.back().op |= kSoftRegionEnd;
         rr.push_back(make_int2(begin, (int)ins.size()));
     }
     return SMCRT_OK;
@@ -254,6 +256,7 @@ uint64_t shape_key(const smcrt_scene *sc, int precision, const smcrt_grid *g)
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
     mix((uint64_t)precision);
+    mix((uint64_t)sc->stepping);
     mix((uint64_t)sc->nprims);
     mix((uint64_t)sc->nregions);
     mix((uint64_t)sc->nnodes);
@@ -438,6 +441,9 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     if (precision == SMCRT_MIXED) build_cull(sc, cg);
     const size_t o_coff = take(sizeof(int32_t) * cg.off.size());
     const size_t o_clist = take(sizeof(int32_t) * cg.list.size());
+    std::vector<int32_t> segp(sc->stepping == SMCRT_STEP_SEGMENT ? kMaxPrims : 0);
+    const int nseg = segp.empty() ? 0 : hard_region_prims(sc, segp.data());
+    const size_t o_seg = take(sizeof(int32_t) * nseg);
     const size_t total = off;
 
     std::unique_ptr<smcrt_plan> pl(new smcrt_plan());
@@ -489,6 +495,9 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     H.cull_kinv = cg.kinv;
     H.cull_off = cg.region >= 0 ? (const int32_t *)(base + o_coff) : nullptr;
     H.cull_list = cg.region >= 0 ? (const int32_t *)(base + o_clist) : nullptr;
+    H.stepping = sc->stepping;
+    H.nseg = nseg;
+    H.seg_prims = nseg > 0 ? (const int32_t *)(base + o_seg) : nullptr;
     {   // analytic normals when every region's program is short
         int longest = 0;
         for (int r = 0; r < nr; ++r) longest = std::max(longest, rr[r].y - rr[r].x);
@@ -530,6 +539,7 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     std::memcpy(hb.data() + o_r32, reg32.data(), sizeof(float4) * 2 * nr);
     if (!cg.off.empty()) std::memcpy(hb.data() + o_coff, cg.off.data(), sizeof(int32_t) * cg.off.size());
     if (!cg.list.empty()) std::memcpy(hb.data() + o_clist, cg.list.data(), sizeof(int32_t) * cg.list.size());
+    if (nseg > 0) std::memcpy(hb.data() + o_seg, segp.data(), sizeof(int32_t) * nseg);
     pl->dscene = (DevScene *)(base + o_scene);
     pl->cells = (size_t)g->n[0] * g->n[1] * g->n[2];
     if (serving_stream) {

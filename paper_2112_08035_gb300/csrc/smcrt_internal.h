@@ -22,6 +22,41 @@ constexpr int kAnalyticNormalMaxInstr = 4;
 constexpr int kCullMinPrims = 16;
 constexpr int kCullGrid = 16;   // packet kernels are compiled for <= 128 threads per block
 
+// Segment stepping: the last instruction of a region whose program contains
+// a smooth union ("soft" region: its boundary is not made of primitive
+// boundaries, so only |d| bounds it) carries this bit in Instr.op.
+constexpr int32_t kSoftRegionEnd = 0x10000;
+
+inline bool region_is_soft(const smcrt_scene *sc, int r)
+{
+    const smcrt_region &R = sc->regions[r];
+    for (int i = 0; i < R.node_count; ++i)
+        if (sc->nodes[R.node_begin + i].op == SMCRT_OP_SMOOTH_UNION) return true;
+    return false;
+}
+
+// Distinct primitives of the hard (not soft) regions, in first-use order:
+// the primitives whose offset surfaces bound a segment-stepping move.
+// Writes at most kMaxPrims indices; no allocation.
+inline int hard_region_prims(const smcrt_scene *sc, int32_t *out)
+{
+    uint64_t seen[kMaxPrims / 64] = {};
+    int n = 0;
+    for (int r = 0; r < sc->nregions; ++r) {
+        if (region_is_soft(sc, r)) continue;
+        const smcrt_region &R = sc->regions[r];
+        for (int i = 0; i < R.node_count; ++i) {
+            const smcrt_csg_node &nd = sc->nodes[R.node_begin + i];
+            if (nd.op != SMCRT_OP_PRIM || nd.prim < 0 || nd.prim >= kMaxPrims) continue;
+            const uint64_t bit = 1ull << (nd.prim & 63);
+            if (seen[nd.prim >> 6] & bit) continue;
+            seen[nd.prim >> 6] |= bit;
+            out[n++] = nd.prim;
+        }
+    }
+    return n;
+}
+
 // Device instruction (compiled CSG program).  op: 0 push primitive;
 // 1 union, 2 smooth union, 3 intersect, 4 subtract.  prim >= 0 with a
 // binary op means "combine the stack top (left) with this primitive
@@ -69,6 +104,9 @@ struct DevScene {
     float cull_kinv;
     const int32_t *cull_off;  // G^3 + 1 prefix offsets into cull_list
     const int32_t *cull_list; // primitive indices, in the region's fold order
+    // Segment stepping (enum smcrt_stepping): the primitives of hard regions
+    const int32_t *seg_prims;
+    int32_t stepping, nseg;
     float h32;                // FP32 central-difference step for normals
     int64_t max_steps;
     // source

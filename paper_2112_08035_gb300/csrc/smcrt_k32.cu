@@ -16,6 +16,30 @@ namespace {
 
 constexpr float kGrazeCos = 0.05f;    // FP64 refinement below this |cos_i|
 constexpr float kCritBand = 0.01f;    // ... and within this band of sin^2_t = 1
+constexpr float kLandCos = 0.25f;     // line-preserving landing down to this |cos| of the new direction
+
+// Where a packet lands after a Fresnel decision at the surface point q.  The
+// decision is taken on the ray through q, so the packet continues on that
+// ray: it moves along its new direction v until it is a (= 2 delta32) from
+// the tangent plane, on the chosen side sd = +-1 along n.  A push along n
+// instead would shift the ray sideways by a sin(theta) at every event; at
+// concentric spheres that shift accumulates in r sin(theta) (the quantity
+// Snell's law conserves between them), and a packet near the critical angle
+// of a glass shell drifts into total internal reflection at both walls and
+// stays there.  Directions within kLandCos of the plane move a / kLandCos
+// along v and the rest of the distance along n, so no landing moves more than
+// 4 a.  Like a push along n, the landing puts the packet a deeper without
+// drawing an interaction over the way there.
+__device__ __forceinline__ void land32(float qx, float qy, float qz, float vx, float vy, float vz, float nx,
+                                       float ny, float nz, float a, float sd, float &px, float &py, float &pz)
+{
+    const float c = fabsf(vx * nx + vy * ny + vz * nz);
+    const float s = __fdividef(a, fmaxf(c, kLandCos));
+    const float rest = sd * fmaxf(a - s * c, 0.f);
+    px = qx + s * vx + rest * nx;
+    py = qy + s * vy + rest * ny;
+    pz = qz + s * vz + rest * nz;
+}
 
 __device__ __forceinline__ float hg_cos32(float g, float xi)
 {
@@ -65,7 +89,8 @@ __device__ __forceinline__ double region_n64(const DevScene &S, int r)
 // forward differences d(p + delta e_a) for the normal (truncation error
 // delta * curvature) -- a Newton step onto the surface along that normal,
 // and the Fresnel decision (uniform xi), reflected or refracted direction
-// and push-off, all in FP64.
+// and landing (land32), all in FP64.  A ray tangent in FP64 does not cross:
+// it stays on the near side with its direction unchanged.
 __device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, int rfar, float sg32, uint32_t xiw,
                                       float &px, float &py, float &pz, float &ux, float &uy, float &uz,
                                       float nx32, float ny32, float nz32)
@@ -116,8 +141,15 @@ __device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, i
         sx = e;
     }
     const double il = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
-    ux = (float)(vx * il); uy = (float)(vy * il); uz = (float)(vz * il);
-    px = (float)(qx + sx * nx); py = (float)(qy + sx * ny); pz = (float)(qz + sx * nz);
+    vx *= il; vy *= il; vz *= il;
+    ux = (float)vx; uy = (float)vy; uz = (float)vz;
+    // line-preserving landing (land32), in FP64
+    const double a = fabs(e), cv = fabs(vx * nx + vy * ny + vz * nz);
+    const double s = a / fmax(cv, (double)kLandCos);
+    const double rest = (sx > 0.0 ? 1.0 : -1.0) * fmax(a - s * cv, 0.0);
+    px = (float)(qx + s * vx + rest * nx);
+    py = (float)(qy + s * vy + rest * ny);
+    pz = (float)(qz + s * vz + rest * nz);
 }
 
 // Per-warp shared state: the staged scene and the warp's tally slots.
@@ -144,7 +176,15 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
 
     bool alive = false, retired = false;
     float px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0, w = 0, tau = 0;
-    float qx = 0, qy = 0, qz = 0;        // NRM: gradient; FAR / NEAR: surface point
+    float qx = 0, qy = 0, qz = 0;        // FAR / NEAR: surface point; TRACE: crawl anchor
+    // Crawl: a packet within delta32 of a surface that it is leaving takes
+    // forced steps of delta32 along u.  Adding the same small step to an
+    // FP32 position again and again rounds the same way every time, and over
+    // a few hundred steps (a near-tangent departure from a concave wall) the
+    // bias carries the packet across the wall unnoticed.  So the crawl keeps
+    // an anchor q and its length cs along u, and places the packet at
+    // q + cs u (one rounding, whatever the step count).  cs < 0: no crawl.
+    float cs = -1.f;
     float nx = 0, ny = 0, nz = 0, cdot = 0, fplus = 0, dstar = 0;
     int phase = kTrace, sub = 0, istar = -1, reg = -1, rfar = -1;
     int nsteps = 0;
@@ -181,6 +221,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                         id_lo = d.id_lo; id_hi = d.id_hi; event = d.event;
                         nsteps = (int)d.nsteps; pscat = d.pscat;
                         phase = kTrace;
+                        cs = -1.f;
                         t_acq = (uint32_t)clock();
                         alive = true;
                     }
@@ -234,6 +275,8 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
 
         // ---- 3. classify
         bool move = false, fresnel = false, iter_done = false, nrm_ready = false;
+        bool seg_step = false;                 // a tracing move that segment stepping may lengthen
+        bool crawl = false;                    // a forced step away from a surface
         bool fin = false;                      // the packet ends this iteration
         long long fin_R = 0, fin_T = 0, fin_K = 0;
         float L = 0.f;
@@ -253,7 +296,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                         istar = E.istar;
                         dstar = E.dstar;
                         if (S.analytic_nrm) {              // gradient of a short program, now
-                            grad_surface32(S, istar, px, py, pz, qx, qy, qz);
+                            grad_surface32(S, istar, px, py, pz, nx, ny, nz);
                             nrm_ready = true;
                         } else {                           // six probes in the next iterations
                             phase = kNrm;
@@ -262,6 +305,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                     } else {
                         L = E.dmin - 0.5f * delta;
                         move = true;
+                        seg_step = S.stepping == SMCRT_STEP_SEGMENT;
                     }
                 }
             } else if (phase == kNrm) {
@@ -271,7 +315,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 } else {
                     const float gg = fplus - f;
                     const int a = sub >> 1;
-                    if (a == 0) qx = gg; else if (a == 1) qy = gg; else qz = gg;
+                    if (a == 0) nx = gg; else if (a == 1) ny = gg; else nz = gg;
                 }
                 if (++sub == 6) nrm_ready = true;
             } else if (phase == kFar) {
@@ -292,17 +336,18 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
 
         // ---- 3b. a normal is ready (analytic, or after the sixth probe)
         if (nrm_ready) {
-            const float l2 = qx * qx + qy * qy + qz * qz;
+            const float l2 = nx * nx + ny * ny + nz * nz;
             bool approaching = false;
             if (l2 > 0.f) {
                 const float il = rsqrtf(l2);
-                nx = qx * il; ny = qy * il; nz = qz * il;
+                nx *= il; ny *= il; nz *= il;
                 cdot = ux * nx + uy * ny + uz * nz;
                 approaching = (cdot > 0.f && dstar < 0.f) || (cdot < 0.f && dstar >= 0.f);
             }
             if (!approaching) {
                 L = delta;                          // forced step along u
                 move = true;
+                crawl = true;
             } else if (istar < 0) {                 // leaves the volume: R or T
                 const long long v = fx32(w);
                 if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
@@ -311,6 +356,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             } else {
                 wadd(wa, kIntf, 1);
                 qx = px - dstar * nx; qy = py - dstar * ny; qz = pz - dstar * nz;
+                cs = -1.f;
                 phase = kFar;
             }
         }
@@ -324,10 +370,21 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 mu_t = RG.x; imu_t = RG.y;
             }
             interact = mu_t > 0.f && tau < mu_t * L;
+            if (seg_step && !interact) {           // segment stepping: a longer move along u
+                L = fmaxf(L, segment_bound32(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
+                interact = mu_t > 0.f && tau < mu_t * L;
+            }
             const float seg = interact ? tau * imu_t : L;
             long long *const flu = (long long *)jc->flu;
             if (flu) tally32(S, flu, px, py, pz, ux, uy, uz, seg, w, &npieces);
-            px += seg * ux; py += seg * uy; pz += seg * uz;
+            if (crawl) {
+                if (cs < 0.f) { qx = px; qy = py; qz = pz; cs = 0.f; }
+                cs += seg;
+                px = qx + cs * ux; py = qy + cs * uy; pz = qz + cs * uz;
+            } else {
+                px += seg * ux; py += seg * uy; pz += seg * uz;
+                cs = -1.f;
+            }
             tau -= mu_t * seg;
             phase = kTrace;
             iter_done = true;
@@ -371,6 +428,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             tau = -__logf(u01_32(r.w));
             w = 1.f;
             nsteps = 0; pA = 0; pG = 0; pscat = 0;
+            cs = -1.f;
             phase = kTrace;
         }
         if (interact) {                            // implicit capture, HG, roulette
@@ -380,6 +438,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             w = wn;
             scatter32(ux, uy, uz, hg_cos32(RG.w, u01_32(r.x)), u01_32(r.y));
             pscat += 1u;
+            cs = -1.f;
             tau = -__logf(u01_32(r.w));
             if (w < (float)kWRoulette) {
                 if (u01_32(r.z) <= (float)(1.0 / kRouletteM)) {
@@ -412,18 +471,18 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                     const float rp = __fdividef(n1 * ct - n2 * ci, n1 * ct + n2 * ci);
                     R = 0.5f * (rs * rs + rp * rp);
                 }
-                const float e = 2.f * delta * sg;
+                float sd;
                 if (u01_32(r.x) <= R) {
                     const float c2 = 2.f * cdot;
                     ux -= c2 * nx; uy -= c2 * ny; uz -= c2 * nz;
-                    normalise32(ux, uy, uz);
-                    px = qx - e * nx; py = qy - e * ny; pz = qz - e * nz;
+                    sd = -sg;
                 } else {
                     const float k = sg * (eta * ci - ct);
                     ux = eta * ux - k * nx; uy = eta * uy - k * ny; uz = eta * uz - k * nz;
-                    normalise32(ux, uy, uz);
-                    px = qx + e * nx; py = qy + e * ny; pz = qz + e * nz;
+                    sd = sg;
                 }
+                normalise32(ux, uy, uz);
+                land32(qx, qy, qz, ux, uy, uz, nx, ny, nz, 2.f * delta, sd, px, py, pz);
             }
             phase = kTrace;
             iter_done = true;
@@ -451,8 +510,9 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 recs[id - jc->begin] = r;
             }
         }
-        // ---- park a straggler at a trace boundary (serving rounds only)
-        if (alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
+        // ---- park a straggler at a trace boundary (serving rounds only); not
+        // in a crawl, whose anchor is not part of the parked state
+        if (alive && phase == kTrace && cs < 0.f && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
             const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);

@@ -162,6 +162,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
 
         // ---- 3. classify
         bool move = false, fresnel = false, iter_done = false;
+        bool seg_step = false;                 // a tracing move that segment stepping may lengthen
         bool fin = false;                      // the packet ends this iteration
         long long fin_R = 0, fin_T = 0, fin_K = 0;
         double L = 0.0, R = 1.0, ct = 0.0, n1 = 0.0, n2 = 0.0;
@@ -184,6 +185,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
                     } else {
                         L = E.dmin - 0.5 * delta;        // stop short of the surface
                         move = true;
+                        seg_step = S.stepping == SMCRT_STEP_SEGMENT;
                     }
                 }
             } else if (phase == kNrm) {
@@ -261,6 +263,10 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
             double mu_t = 0.0;
             if (reg >= 0) mu_t = __ldg(S.reg64 + 8 * reg + 4);
             interact = mu_t > 0.0 && tau < mu_t * L;
+            if (seg_step && !interact) {           // segment stepping: a longer move along u
+                L = fmax(L, segment_bound64(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
+                interact = mu_t > 0.0 && tau < mu_t * L;
+            }
             const double seg = interact ? tau / mu_t : L;
             long long *const flu = (long long *)jc->flu;
             if (flu) tally64(S, flu, px, py, pz, ux, uy, uz, seg, w, &npieces);

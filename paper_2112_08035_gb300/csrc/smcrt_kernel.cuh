@@ -151,8 +151,9 @@ __device__ __forceinline__ long long fx32(float x)
 // ---------------------------------------------------------------------------
 // Scene evaluation.  Instr.op packs op | (primitive kind << 8).
 // ---------------------------------------------------------------------------
-struct Eval64 { double dmin, dstar, dsel, dbox; int istar, region; };
-struct Eval32 { float dmin, dstar, dsel, dbox; int istar, region; };
+// dsoft: min |d| over soft regions (segment stepping), +inf if none.
+struct Eval64 { double dmin, dstar, dsel, dbox, dsoft; int istar, region; };
+struct Eval32 { float dmin, dstar, dsel, dbox, dsoft; int istar, region; };
 
 __device__ __forceinline__ double box64(double x, double y, double z, double cx, double cy, double cz,
                                         double hx, double hy, double hz)
@@ -241,7 +242,7 @@ __device__ __forceinline__ double run_prog64(const DevScene &S, int i0, int i1, 
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int i = i0; i < i1; ++i) {
         const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
-        const int op = ins.x & 0xff, kind = ins.x >> 8;
+        const int op = ins.x & 0xff, kind = (ins.x >> 8) & 0xff;
         double v = 0.0;
         if (ins.y >= 0) v = prim64(S, kind, ins.y, x, y, z);
         if (op == 0) {
@@ -260,6 +261,7 @@ __device__ __forceinline__ double run_prog64(const DevScene &S, int i0, int i1, 
             if (d < 0.0) E->region = ins.z;
             const double ad = fabs(d);
             if (ad < E->dmin) { E->dmin = ad; E->istar = ins.z; E->dstar = d; }
+            if ((ins.x & kSoftRegionEnd) && ad < E->dsoft) E->dsoft = ad;
             if (ins.z == sel) E->dsel = d;
         }
     }
@@ -273,7 +275,7 @@ __device__ __forceinline__ float run_prog32(const DevScene &S, int i0, int i1, f
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     for (int i = i0; i < i1; ++i) {
         const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
-        const int op = ins.x & 0xff, kind = ins.x >> 8;
+        const int op = ins.x & 0xff, kind = (ins.x >> 8) & 0xff;
         float v = 0.f;
         if (ins.y >= 0) v = prim32(S, kind, ins.y, x, y, z);
         if (op == 0) {
@@ -292,6 +294,7 @@ __device__ __forceinline__ float run_prog32(const DevScene &S, int i0, int i1, f
             if (d < 0.f) E->region = ins.z;
             const float ad = fabsf(d);
             if (ad < E->dmin) { E->dmin = ad; E->istar = ins.z; E->dstar = d; }
+            if ((ins.x & kSoftRegionEnd) && ad < E->dsoft) E->dsoft = ad;
             if (ins.z == sel) E->dsel = d;
         }
     }
@@ -303,6 +306,7 @@ __device__ __forceinline__ Eval64 scene_eval64(const DevScene &S, double x, doub
 {
     Eval64 E;
     E.dmin = __longlong_as_double(0x7ff0000000000000LL);
+    E.dsoft = E.dmin;
     E.dstar = 0.0; E.dsel = 0.0; E.istar = -1; E.region = -1;
     run_prog64<true>(S, 0, S.ninstr, x, y, z, sel, &E);
     const double db = box64(x, y, z, S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2]);
@@ -335,11 +339,12 @@ __device__ __forceinline__ float culled_region32(const DevScene &S, float x, flo
     return fminf(acc, S.cull_rmax);
 }
 
-__device__ __forceinline__ void region_end32(Eval32 *E, int r, float d, int sel)
+__device__ __forceinline__ void region_end32(Eval32 *E, int r, float d, int sel, bool soft)
 {
     if (d < 0.f) E->region = r;
     const float ad = fabsf(d);
     if (ad < E->dmin) { E->dmin = ad; E->istar = r; E->dstar = d; }
+    if (soft && ad < E->dsoft) E->dsoft = ad;
     if (r == sel) E->dsel = d;
 }
 
@@ -347,13 +352,14 @@ __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float
 {
     Eval32 E;
     E.dmin = __int_as_float(0x7f800000);
+    E.dsoft = E.dmin;
     E.dstar = 0.f; E.dsel = 0.f; E.istar = -1; E.region = -1;
     if (S.cull_region < 0) {
         run_prog32<true>(S, 0, S.ninstr, x, y, z, sel, &E);
     } else {   // regions in index order: before, the culled one, after
         const int2 rr = __ldg(S.rrange + S.cull_region);
         run_prog32<true>(S, 0, rr.x, x, y, z, sel, &E);
-        region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel);
+        region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, S.cull_op == 2);
         run_prog32<true>(S, rr.y, S.ninstr, x, y, z, sel, &E);
     }
     const float db = box32(x, y, z, S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2]);
@@ -445,7 +451,7 @@ static __device__ __noinline__ float grad_surface32(const DevScene &S, int r, fl
     int sp = 0;
     for (int i = rr.x; i < rr.y; ++i) {
         const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
-        const int op = ins.x & 0xff, kind = ins.x >> 8;
+        const int op = ins.x & 0xff, kind = (ins.x >> 8) & 0xff;
         float a = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
         if (ins.y >= 0) a = prim_grad32(S, kind, ins.y, x, y, z, ax, ay, az);
         if (op == 0) {
@@ -469,6 +475,163 @@ __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, 
     if (r < 0) return box64(x, y, z, S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2]);
     const int2 rr = __ldg(S.rrange + r);
     return run_prog64<false>(S, rr.x, rr.y, x, y, z, -2, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Segment stepping (scene option; Sec. 5 names segment tracing for packets
+// moving nearly parallel to a surface).  Bound on the move along u: for each
+// sphere and box of a hard-CSG region, the distance along the ray to its
+// surface offset by delta/2 (grown when p is outside, shrunk when inside),
+// over which the primitive's |SDF| stays above delta/2 and its sign cannot
+// change; |d| - delta/2 for soft regions (dsoft) and capsules; the exit of
+// the bounding box shrunk by delta/2.  The caller moves max(d_min - delta/2,
+// bound).  FP64: the reference's operations in its order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double seg_sphere64(const double *P, double d, double px, double py, double pz,
+                                               double ux, double uy, double uz, double dh)
+{
+    const double rr = d > 0.0 ? __ldg(P + 3) + dh : __ldg(P + 3) - dh;
+    const double ox = px - __ldg(P), oy = py - __ldg(P + 1), oz = pz - __ldg(P + 2);
+    const double b = ox * ux + oy * uy + oz * uz;
+    const double cc = ox * ox + oy * oy + oz * oz - rr * rr;
+    const double disc = b * b - cc;
+    double t;
+    if (d > 0.0) {                       // outside: entry of the grown sphere (near root)
+        if (b >= 0.0 || disc < 0.0) return __longlong_as_double(0x7ff0000000000000LL);
+        t = cc / (sqrt(disc) - b);
+    } else {                             // inside: exit of the shrunk sphere
+        if (disc < 0.0) return 0.0;
+        if (b > 0.0) t = -cc / (b + sqrt(disc));
+        else t = sqrt(disc) - b;
+    }
+    return t > 0.0 ? t : 0.0;
+}
+
+__device__ __forceinline__ double seg_box64(double cx, double cy, double cz, double hx, double hy, double hz,
+                                            double d, double px, double py, double pz, double ux, double uy,
+                                            double uz, double dh)
+{
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const double e = d > 0.0 ? dh : -dh;
+    const double c[3] = {cx, cy, cz}, h[3] = {hx, hy, hz}, p[3] = {px, py, pz}, u[3] = {ux, uy, uz};
+    double tn = -inf, tf = inf;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double lo = c[a] - (h[a] + e), hi = c[a] + (h[a] + e);
+        if (u[a] != 0.0) {
+            const double t0 = (lo - p[a]) / u[a], t1 = (hi - p[a]) / u[a];
+            tn = fmax(tn, fmin(t0, t1));
+            tf = fmin(tf, fmax(t0, t1));
+        } else if (p[a] < lo || p[a] > hi) {
+            return d > 0.0 ? inf : 0.0;
+        }
+    }
+    if (d > 0.0) {                       // outside: entry of the grown box
+        if (tn > tf || tf < 0.0) return inf;
+        return tn > 0.0 ? tn : 0.0;
+    }
+    return tf > 0.0 ? tf : 0.0;          // inside: exit of the shrunk box
+}
+
+static __device__ __noinline__ double segment_bound64(const DevScene &S, double dsoft, double dbox, double px,
+                                                      double py, double pz, double ux, double uy, double uz)
+{
+    const double dh = 0.5 * S.delta;
+    double t = dsoft - dh;
+    for (int j = 0; j < S.nseg; ++j) {
+        const int i = __ldg(S.seg_prims + j);
+        const int kind = __ldg(S.pkind + i);
+        const double d = prim64(S, kind, i, px, py, pz);
+        double b;
+        if (!(fabs(d) > dh)) {
+            b = 0.0;
+        } else if (kind == 0) {
+            b = seg_sphere64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, dh);
+        } else if (kind == 1) {
+            const double *P = S.p64 + 8 * i;
+            b = seg_box64(__ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5), d, px,
+                          py, pz, ux, uy, uz, dh);
+        } else {
+            b = fabs(d) - dh;            // capsule: isotropic
+        }
+        t = fmin(t, b);
+    }
+    return fmin(t, seg_box64(S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2], dbox, px, py, pz, ux,
+                             uy, uz, dh));
+}
+
+// FP32 (mixed): the same bounds with reciprocal directions.
+__device__ __forceinline__ float seg_sphere32(float4 A, float d, float px, float py, float pz, float ux, float uy,
+                                              float uz, float dh)
+{
+    const float rr = d > 0.f ? A.w + dh : A.w - dh;
+    const float ox = px - A.x, oy = py - A.y, oz = pz - A.z;
+    const float b = ox * ux + oy * uy + oz * uz;
+    const float cc = ox * ox + oy * oy + oz * oz - rr * rr;
+    const float disc = b * b - cc;
+    float t;
+    if (d > 0.f) {
+        if (b >= 0.f || disc < 0.f) return __int_as_float(0x7f800000);
+        t = cc / (sqrtf(disc) - b);
+    } else {
+        if (disc < 0.f) return 0.f;
+        t = b > 0.f ? -cc / (b + sqrtf(disc)) : sqrtf(disc) - b;
+    }
+    return t > 0.f ? t : 0.f;
+}
+
+__device__ __forceinline__ float seg_box32(float cx, float cy, float cz, float hx, float hy, float hz, float d,
+                                           float px, float py, float pz, float ux, float uy, float uz, float iux,
+                                           float iuy, float iuz, float dh)
+{
+    const float inf = __int_as_float(0x7f800000);
+    const float e = d > 0.f ? dh : -dh;
+    const float c[3] = {cx, cy, cz}, h[3] = {hx, hy, hz}, p[3] = {px, py, pz}, u[3] = {ux, uy, uz};
+    const float iu[3] = {iux, iuy, iuz};
+    float tn = -inf, tf = inf;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = c[a] - (h[a] + e), hi = c[a] + (h[a] + e);
+        if (u[a] != 0.f) {
+            const float t0 = (lo - p[a]) * iu[a], t1 = (hi - p[a]) * iu[a];
+            tn = fmaxf(tn, fminf(t0, t1));
+            tf = fminf(tf, fmaxf(t0, t1));
+        } else if (p[a] < lo || p[a] > hi) {
+            return d > 0.f ? inf : 0.f;
+        }
+    }
+    if (d > 0.f) {
+        if (tn > tf || tf < 0.f) return inf;
+        return tn > 0.f ? tn : 0.f;
+    }
+    return tf > 0.f ? tf : 0.f;
+}
+
+static __device__ __noinline__ float segment_bound32(const DevScene &S, float dsoft, float dbox, float px,
+                                                     float py, float pz, float ux, float uy, float uz)
+{
+    const float dh = 0.5f * S.delta32;
+    const float iux = 1.0f / ux, iuy = 1.0f / uy, iuz = 1.0f / uz;
+    float t = dsoft - dh;
+    for (int j = 0; j < S.nseg; ++j) {
+        const int i = __ldg(S.seg_prims + j);
+        const int kind = __ldg(S.pkind + i);
+        const float d = prim32(S, kind, i, px, py, pz);
+        float b;
+        if (!(fabsf(d) > dh)) {
+            b = 0.f;
+        } else if (kind == 0) {
+            b = seg_sphere32(__ldg(S.p32 + 2 * i), d, px, py, pz, ux, uy, uz, dh);
+        } else if (kind == 1) {
+            const float4 A = __ldg(S.p32 + 2 * i), B = __ldg(S.p32 + 2 * i + 1);
+            b = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, px, py, pz, ux, uy, uz, iux, iuy, iuz, dh);
+        } else {
+            b = fabsf(d) - dh;
+        }
+        t = fminf(t, b);
+    }
+    return fminf(t, seg_box32(S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2], dbox, px,
+                              py, pz, ux, uy, uz, iux, iuy, iuz, dh));
 }
 
 // ---------------------------------------------------------------------------

@@ -118,6 +118,7 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
         }
         if (depth != 1) return SMCRT_ERR_BAD_SCENE;
         ins[ni - 1].region = r;
+        if (region_is_soft(sc, r)) ins[ni - 1].op |= kSoftRegionEnd;
         rr[r] = make_int2(begin, ni);
     }
     const int np = sc->nprims, nr = sc->nregions;
@@ -133,6 +134,9 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     const size_t o_rr = take(sizeof(int2) * nr);
     const size_t o_r64 = take(sizeof(double) * 8 * nr);
     const size_t o_r32 = take(sizeof(float4) * 2 * nr);
+    int32_t segp[kMaxPrims];
+    const int nseg = sc->stepping == SMCRT_STEP_SEGMENT ? hard_region_prims(sc, segp) : 0;
+    const size_t o_seg = take(sizeof(int32_t) * nseg);
     if (kImageOff + off > kNoAllocScratchBytes) return SMCRT_ERR_NO_MEMORY;
     std::memset(img, 0, off);
 
@@ -174,6 +178,7 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     std::memcpy(img + o_ins, ins, sizeof(Instr) * ni);
     std::memcpy(img + o_k64, k64, sizeof(double) * ni);
     std::memcpy(img + o_rr, rr, sizeof(int2) * nr);
+    if (nseg > 0) std::memcpy(img + o_seg, segp, sizeof(int32_t) * nseg);
 
     unsigned char *base = dev_base + kImageOff;   // device addresses of the tables
     DevScene H;
@@ -202,6 +207,9 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     H.ambient_n = sc->ambient_n;
     H.ambient_n32 = (float)sc->ambient_n;
     H.cull_region = -1;   // no culling grid in the fixed scratch
+    H.stepping = sc->stepping;
+    H.nseg = nseg;
+    H.seg_prims = nseg > 0 ? (const int32_t *)(base + o_seg) : nullptr;
     {
         int longest = 0;
         for (int r = 0; r < nr; ++r) longest = (rr[r].y - rr[r].x) > longest ? (rr[r].y - rr[r].x) : longest;

@@ -79,6 +79,27 @@ def test_fp64_bitexact_small(ctx, factory, n):
         assert np.array_equal(rg[f], ro[f]), f
 
 
+@pytest.mark.parametrize("factory,n", SMALL, ids=[f.__name__ for f, _ in SMALL])
+def test_fp64_bitexact_segment_stepping(ctx, factory, n):
+    # segment stepping (longer moves bounded along the ray): the FP64 kernel
+    # still performs the reference's operations, so the bits agree
+    wl = factory().with_packets(n).with_stepping(W.SEGMENT)
+    fo, to, ro = O.run(wl, records=True)
+    fg, tg, rg = run_gpu(ctx, wl, "fp64", records=True)
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+    for f in ("R", "T", "A", "killed", "gain", "scatters", "steps"):
+        assert np.array_equal(rg[f], ro[f]), f
+
+
+def test_fp64_bitexact_segment_config0_full_size(ctx):
+    wl = W.sphere_pencil().with_stepping(W.SEGMENT)
+    fo, to, _ = O.run(wl)
+    fg, tg = run_gpu(ctx, wl, "fp64")
+    assert_exact(tg, to)
+    assert np.array_equal(fg, fo)
+
+
 def test_fp64_bitexact_config0_full_size(ctx):
     # the plain-FP64 sphere workload at its full 1e5 packets, 50^3 grid
     wl = W.sphere_pencil()
@@ -128,12 +149,16 @@ MIXED = [
 ]
 
 
+@pytest.mark.parametrize("stepping", [W.SPHERE_TRACING, W.SEGMENT])
 @pytest.mark.parametrize("factory,ng,no", MIXED, ids=[f.__name__ for f, _, _ in MIXED])
-def test_mixed_matches_oracle_statistically(ctx, factory, ng, no):
+def test_mixed_matches_oracle_statistically(ctx, factory, ng, no, stepping):
+    # the oracle always runs the paper's plain sphere tracing; the GPU runs
+    # mixed precision with either step rule
     wl = factory()
     fo, to, ro = O.run(wl.with_packets(no), records=True)
     # disjoint packet ids for the GPU sample: independent estimates
-    fg, tg, rg = run_gpu(ctx, wl.with_packets(ng), "mixed", records=True, id_begin=10_000_000)
+    fg, tg, rg = run_gpu(ctx, wl.with_packets(ng).with_stepping(stepping), "mixed", records=True,
+                         id_begin=10_000_000)
     for key in ("R", "T", "A"):
         _zcheck(rg, ro, key)
     # fluence: relative L2 difference of the normalised maps is consistent
@@ -148,6 +173,22 @@ def test_mixed_matches_oracle_statistically(ctx, factory, ng, no):
     # energy closes per packet (FP32 weights: relative 1e-5 per packet)
     bal = (rg["R"] + rg["T"] + rg["A"] + rg["killed"] - rg["gain"]) / FX
     assert np.all(np.abs(bal - 1.0) < 1e-4)
+
+
+@pytest.mark.parametrize("stepping", [W.SPHERE_TRACING, W.SEGMENT])
+def test_mixed_glass_shell_traps_no_packet(ctx, stepping):
+    # Between two concentric spheres Snell's law conserves n r sin(theta), so
+    # no packet that enters the clear glass shell from the air or the liquid
+    # can meet total internal reflection at both walls.  Two FP32 effects once
+    # trapped about one packet in 1e6 there until the step cap: pushes along
+    # the normal that shifted r sin(theta) the same way at every bounce, and
+    # crawls (forced steps away from a wall) whose identical FP32 increments
+    # rounded the same way until the packet crossed the wall unnoticed.  At
+    # 1e7 packets neither step rule may hit the cap.
+    wl = W.glass_container(10_000_000).with_stepping(stepping)
+    _, t = run_gpu(ctx, wl, "mixed")
+    assert t["packets"] == wl.npackets
+    assert t["max_steps_hit"] == 0, t["max_steps_hit"]
 
 
 def test_register_variants_identical(ctx):
