@@ -3,11 +3,12 @@
 Workload (one "step"): the three-layer slab -- three box SDF layers 0.1 /
 0.2 / 1.0 cm thick (mu_a 0.1-2, mu_s 10-100 /cm, g 0.8-0.95, n 1.3-1.5),
 pencil beam, 1e7 packets, 100^3 int64 fluence grid -- in the mixed
-precision mode (FP32 tracing, FP64 interface refinement).  ``value`` is
-packets/s with the scene resident on the device; the JSON line also carries
-the plain-FP64 mode on the same workload, R/T/A against the FP64 CPU
-oracle, the served mix's p50/p99 job latency, the roofline of the packet
-kernel, and the oracle timed on the host cores.
+precision mode (FP32 tracing, FP64 interface refinement) with segment
+stepping (``--stepping``).  ``value`` is packets/s with the scene resident on
+the device; the JSON line also carries the mixed mode with plain sphere
+tracing and the plain-FP64 mode (sphere tracing) on the same workload, R/T/A
+of each against the FP64 CPU oracle, the served mix's p50/p99 job latency,
+the roofline of the packet kernel, and the oracle timed on the host cores.
 
 Multi-GPU (torchrun): packets are independent, so each rank runs its own
 1e7-packet block of ids (weak scaling, no data-path collective); the step
@@ -178,7 +179,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = W.three_layer_slab(precision="fp64")
+    wl = W.three_layer_slab(precision="fp64").with_stepping(args.stepping)
     import oracle as O
     O.build()
     threads = os.cpu_count() or 1
@@ -200,7 +201,7 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "three_layer_slab (1e7 packets, 100^3 grid), sampled",
+            "config": {"workload": f"three_layer_slab (1e7 packets, 100^3 grid, {args.stepping} stepping), sampled",
                        "sample_packets_per_step": n},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} packets of three_layer_slab per step (ids disjoint per step)"},
@@ -261,6 +262,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="precision of the timed leg (the headline is mixed)")
+    ap.add_argument("--stepping", default=W.SEGMENT, choices=[W.SEGMENT, W.SPHERE_TRACING],
+                    help="step rule of the timed leg (the headline uses segment stepping)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -277,7 +280,8 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     ctx = smc.Context(local)
-    wl = W.three_layer_slab(args.packets, precision=args.precision)
+    wl = W.three_layer_slab(args.packets, precision=args.precision).with_stepping(args.stepping)
+    wl_plain = wl.with_stepping(W.SPHERE_TRACING)
     g = wl.grid
     from paper_2112_08035_gb300.distributed import shard_range
     id0, _ = shard_range(rank, world, args.packets * world)   # this rank's block of ids
@@ -333,7 +337,9 @@ def main():
            "dtype": "f32+f64 (mixed; int64 tallies)" if args.precision == "mixed" else "f64 (int64 tallies)",
            "data": "synthetic",
            "config": {"workload": f"three_layer_slab: 3 box-SDF layers, pencil beam, {args.packets:.0e} packets "
-                                  f"per GPU, 100^3 int64 fluence grid, {args.precision} precision",
+                                  f"per GPU, 100^3 int64 fluence grid, {args.precision} precision, "
+                                  f"{args.stepping} stepping",
+                      "stepping": args.stepping,
                       "packets_per_step": args.packets * world, "l2": "flushed between timed steps (256 MB write)",
                       "launch": {"blocks": tuned[0], "threads": tuned[1], "register_variant": tuned[2],
                                  "chosen_by": "smcrt_plan_autotune"}},
@@ -361,10 +367,34 @@ def main():
     out["counters_per_packet"]["refined_fraction_of_fresnel"] = (
         totals_mixed["refined"] / max(1, totals_mixed["fresnel"]))
 
+    def timed_leg(wleg, precision, nsteps, tune):
+        p = ctx.plan(wleg, precision)
+        p.autotune(tune)
+        step(min(args.packets, 1_000_000), p, wleg.seed, id0)
+        torch.cuda.synchronize()
+        evs = []
+        for i in range(nsteps):
+            l2_flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(args.packets, p, wleg.seed, id0)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        p.close()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / nsteps, smc.totals_from_tensor(tot)
+
     if not args.quick:
-        # ---- plain FP64 mode on the same workload ---------------------------
-        log(f"mixed {value:.3e} packets/s; timing the FP64 mode")
-        plan64 = ctx.plan(wl, "fp64")
+        # ---- mixed precision with plain sphere tracing (the paper's step) ---
+        totals_st = None
+        if args.stepping != W.SPHERE_TRACING and args.precision == "mixed":
+            log(f"mixed {value:.3e} packets/s; timing mixed with sphere tracing")
+            t_st, totals_st = timed_leg(wl_plain, "mixed", 3, min(args.packets, 2_000_000))
+            out["mixed_sphere_tracing"] = {"value": args.packets / t_st, "unit": UNIT, "ms_per_step": 1e3 * t_st,
+                                           "segment_speedup": t_st / kernel_s}
+        # ---- plain FP64 mode (sphere tracing) on the same workload ----------
+        log("timing the plain FP64 mode")
+        plan64 = ctx.plan(wl_plain, "fp64")
         plan64.autotune(100_000)
         step(min(args.packets, 1_000_000), plan64, wl.seed, id0)
         torch.cuda.synchronize()
@@ -381,6 +411,7 @@ def main():
         totals_fp64 = smc.totals_from_tensor(tot)
         plan64.close()
         out["fp64"] = {"value": args.packets / t64, "unit": UNIT, "ms_per_step": 1e3 * t64,
+                       "stepping": W.SPHERE_TRACING,
                        "mixed_speedup": (args.packets / kernel_s) / (args.packets / t64)}
 
         log(f"fp64 {args.packets / t64:.3e} packets/s; end-to-end leg")
@@ -406,9 +437,12 @@ def main():
         o_pps, o_n, o_threads, o_tot, o_rec = oracle_sample(wl, args.oracle_seconds, id_base=0)
         out["cpu_baseline"] = {"value": o_pps, "unit": UNIT, "cores": o_threads, "kind": "oracle",
                                "sample": f"{o_n} packets (ids 0..{o_n - 1}) of the same three_layer_slab "
-                                         f"workload, FP64, {o_threads} threads"}
+                                         f"workload ({args.stepping} stepping), FP64, {o_threads} threads"}
         acc = {}
-        for name, t in (("mixed", totals_mixed), ("fp64", totals_fp64)):
+        legs = [("mixed", totals_mixed), ("fp64", totals_fp64)]
+        if totals_st is not None:
+            legs.append(("mixed_sphere_tracing", totals_st))
+        for name, t in legs:
             d = {}
             for k in ("R", "T", "A"):
                 ov = o_rec[k] / FX
