@@ -221,7 +221,11 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                         id_lo = d.id_lo; id_hi = d.id_hi; event = d.event;
                         nsteps = (int)d.nsteps; pscat = d.pscat;
                         phase = kTrace;
-                        cs = -1.f;
+                        cs = __uint_as_float(d.pad[0]);
+                        if (cs >= 0.f) {           // parked in a crawl: p holds the anchor
+                            qx = px; qy = py; qz = pz;
+                            px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
+                        }
                         t_acq = (uint32_t)clock();
                         alive = true;
                     }
@@ -380,7 +384,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             if (crawl) {
                 if (cs < 0.f) { qx = px; qy = py; qz = pz; cs = 0.f; }
                 cs += seg;
-                px = qx + cs * ux; py = qy + cs * uy; pz = qz + cs * uz;
+                px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
             } else {
                 px += seg * ux; py += seg * uy; pz += seg * uz;
                 cs = -1.f;
@@ -510,15 +514,18 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 recs[id - jc->begin] = r;
             }
         }
-        // ---- park a straggler at a trace boundary (serving rounds only); not
-        // in a crawl, whose anchor is not part of the parked state
-        if (alive && phase == kTrace && cs < 0.f && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
+        // ---- park a straggler at a trace boundary (serving rounds only).  A
+        // packet in a crawl is parked as its anchor and crawl length, from
+        // which the resume recomputes the same position.
+        if (alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
             const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);
             if (k < dfr->cap) {
                 DeferState &d = dfr->buf[1 - din][k];
-                d.p[0] = px; d.p[1] = py; d.p[2] = pz;
+                const bool in_crawl = cs >= 0.f;
+                d.p[0] = in_crawl ? qx : px; d.p[1] = in_crawl ? qy : py; d.p[2] = in_crawl ? qz : pz;
+                d.pad[0] = __float_as_uint(cs);
                 d.u[0] = ux; d.u[1] = uy; d.u[2] = uz;
                 d.w = w; d.tau = tau;
                 d.pA = pA; d.pG = pG;
