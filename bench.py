@@ -210,11 +210,11 @@ def reference_arm(args):
 
 
 def served_mix(ctx, njobs: int, capacity_pps: float, load: float = 0.8, seed: int = 4,
-               limit_s: float = 240.0):
+               limit_s: float = 240.0, stepping: str = W.SEGMENT):
     """Poisson arrivals of the served mix at ``load`` x measured capacity;
     returns job latencies (submit to completion, measured by the library)
     and the served throughput.  Stops submitting after ``limit_s``."""
-    jobs = W.served_mix(njobs, seed)
+    jobs = W.served_mix(njobs, seed, stepping=stepping)
     rng = np.random.default_rng(seed)
     total = sum(j.npackets for j in jobs)
     mean_gap = (total / njobs) / (capacity_pps * load)
@@ -460,14 +460,15 @@ def main():
         if args.serve_jobs > 0:
             log("serving leg")
             # capacity of the server on this mix: all jobs of a prefix at once
-            cap_jobs = W.served_mix(min(40, args.serve_jobs), 4)
+            cap_jobs = W.served_mix(min(40, args.serve_jobs), 4, stepping=args.stepping)
             t0 = time.perf_counter()
             jids = [ctx.submit(j, "mixed") for j in cap_jobs]
             for jid in jids:
                 ctx.wait(jid, -1.0, fluence=False)
             cap = sum(j.npackets for j in cap_jobs) / (time.perf_counter() - t0)
-            out["serving"] = served_mix(ctx, args.serve_jobs, capacity_pps=cap)
+            out["serving"] = served_mix(ctx, args.serve_jobs, capacity_pps=cap, stepping=args.stepping)
             out["serving"]["capacity_pps"] = cap
+            out["serving"]["stepping"] = args.stepping
     plan.close()
     print(json.dumps(out), flush=True)
     if dist:

@@ -244,7 +244,8 @@ def glass_container(npackets: int = 100_000_000, seed: int = 5, precision: str =
                     npackets, seed, precision)
 
 
-def served_mix(njobs: int = 200, seed: int = 4, budget_lo: float = 1e4, budget_hi: float = 1e7):
+def served_mix(njobs: int = 200, seed: int = 4, budget_lo: float = 1e4, budget_hi: float = 1e7,
+               stepping: str = SPHERE_TRACING):
     """Served mix: jobs drawn from the four scene families with optics redrawn
     uniformly within each family's ranges, log-uniform packet budgets, grid
     sides from {50, 64, 100, 128, 200}, per-job seed splitmix64(seed, j).
@@ -281,7 +282,7 @@ def served_mix(njobs: int = 200, seed: int = 4, budget_lo: float = 1e4, budget_h
         g = w.grid
         w = replace(w, grid=Grid(g.lo, g.hi, (side, side, side)),
                     name=f"mix{j:03d}_{w.name.split('_')[0]}")
-        jobs.append(w)
+        jobs.append(w.with_stepping(stepping))
     return jobs
 
 
