@@ -248,6 +248,73 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
+# Table 2 (Sec. 3.2): the paper's sMCRT timings with a fluence grid, on an
+# AMD Ryzen 9 3950X with 32 threads -- another machine's CPU numbers, quoted
+# as context, not as a target.
+PAPER_TABLE2 = {"jacques": (10_000_000, 33.73), "iso_sphere_tau100": (1_000_000, 75.76)}
+
+
+def paper_cases(ctx, smc, stream, stepping: str):
+    """The paper's timing cases at their sizes (Table 2) in mixed precision:
+    the Jacques et al. slab of Table 1 (both wavelengths; 1e7 photons,
+    200 x 200 x 400 grid) and the isotropic sphere at radial optical depth
+    100 (1e6 photons, 200^3 grid), each one timed launch after a warm-up,
+    with the validation quantity of each (k1 of Eq. 5 fitted to the depth
+    profile, the mean scattering count against Eq. 4)."""
+    import torch
+    out = {}
+    cases = [("jacques_slab_420nm", "jacques", W.jacques_slab(420)),
+             ("jacques_slab_630nm", "jacques", W.jacques_slab(630)),
+             ("iso_sphere_tau100", "iso_sphere_tau100", W.iso_sphere(100.0))]
+    for name, key, wl in cases:
+        wl = wl.with_stepping(stepping)
+        g = wl.grid
+        plan = ctx.plan(wl, "mixed")
+        flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
+        tot = smc.totals_tensor()
+        plan.launch(0, min(wl.npackets, 100_000), wl.seed, flu, tot, None, stream.cuda_stream)
+        torch.cuda.synchronize()
+        flu.zero_()
+        tot.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.launch(0, wl.npackets, wl.seed, flu, tot, None, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        t = smc.totals_from_tensor(tot)
+        n = wl.npackets
+        e = {"photons": n, "grid": list(g.n), "seconds": sec, "packets_per_s": n / sec,
+             "scatters_per_packet": t["scatters"] / n, "max_steps_hit": t["max_steps_hit"]}
+        if key == "jacques":
+            mua, musp = W.JACQUES_OPTICS[int(name.split("_")[-1][:3])]
+            d = W.penetration_depth(mua, musp)
+            nz = g.n[2]
+            phi = flu.sum(dim=(1, 2)).double().cpu().numpy()[::-1]      # surface first
+            z = (np.arange(nz) + 0.5) * (g.hi[2] - g.lo[2]) / nz
+            sel = (z > 4 * d) & (z < 12 * d) & (phi > 0)
+            e["k1_fit"] = float(-np.polyfit(z[sel], np.log(phi[sel]), 1)[0] * d)
+            e["k1_table1"] = 1.00
+            # fluence rate over the grid's 2 x 2 cm relative to the incident
+            # irradiance (photons per cm^2 of the 4 x 4 cm source)
+            area = (g.hi[0] - g.lo[0]) * (g.hi[1] - g.lo[1])
+            dz = (g.hi[2] - g.lo[2]) / nz
+            psi = phi / FX / (area * dz) / (n / (2 * wl.source.radius) ** 2)
+            e["psi_over_incident_at_z"] = {f"{m}delta": float(np.interp(m * d, z, psi)) for m in (1, 2, 4)}
+        else:
+            tau = wl.scene.regions[0].mu_s * wl.scene.prims[0].p[3]
+            want = tau * tau / 2 + tau
+            e["eq4"] = {"mean_scatterings": t["scatters"] / n, "eq4": want,
+                        "rel_diff": (t["scatters"] / n - want) / want}
+        pn, ps = PAPER_TABLE2[key]
+        e["paper_cpu"] = {"photons": pn, "seconds": ps, "packets_per_s": pn / ps,
+                          "machine": "AMD Ryzen 9 3950X, 32 threads (Table 2); context only"}
+        out[name] = e
+        plan.close()
+        del flu
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,6 +326,7 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=100)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="kernel legs only (profiling runs)")
+    ap.add_argument("--no-paper-cases", action="store_true", help="skip the paper's Table 2 timing cases")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="precision of the timed leg (the headline is mixed)")
@@ -455,6 +523,10 @@ def main():
         out["accuracy_vs_oracle"] = acc
         out["accuracy_vs_oracle"]["note"] = ("GPU at 1e7 packets vs oracle sample; z = difference / combined "
                                              "MC sigma. FP64 mode is bit-identical to the oracle packet by packet")
+
+        if not args.no_paper_cases and args.precision == "mixed":
+            log("paper cases (Table 2 sizes)")
+            out["paper_cases"] = paper_cases(ctx, smc, stream, args.stepping)
 
         # ---- served mix: Poisson arrivals at 80% of measured capacity ---------
         if args.serve_jobs > 0:

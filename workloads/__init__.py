@@ -323,6 +323,45 @@ def isotropic_sphere(tau: float, radius: float = 0.5) -> Scene:
                  (-b, -b, -b), (b, b, b))
 
 
+# Table 1 (Sec. 3.1): absorption and reduced scattering per wavelength, for
+# a slab with g = 0.9 and n = 1.38 under air.
+JACQUES_OPTICS = {420: (1.8, 82.0), 630: (0.23, 21.0)}
+
+
+def penetration_depth(mu_a: float, mus_reduced: float) -> float:
+    """delta = 1 / sqrt(3 mu_a (mu_a + mu_s (1 - g))) (Sec. 3.1, with Eq. 5)."""
+    return 1.0 / math.sqrt(3.0 * mu_a * (mu_a + mus_reduced))
+
+
+def jacques_slab(wavelength_nm: int = 630, npackets: int = 10_000_000, seed: int = 6,
+                 precision: str = "mixed", grid_n: Tuple[int, int, int] = (200, 200, 400)) -> Workload:
+    """The semi-infinite slab of the validation against Jacques et al. (Sec.
+    3.1, Table 1) at the size of its timing case (Table 2: 1e7 photons, a
+    200 x 200 x 400 grid): g = 0.9, n = 1.38 under air, light uniformly
+    incident on the surface.  The slab is z in [-40 delta, 0], 100 cm wide;
+    the source is a uniform 4 x 4 cm square just above the surface, going -z;
+    the grid covers x, y in [-1, 1] cm and z in [-16 delta, 0]."""
+    mua, musp = JACQUES_OPTICS[wavelength_nm]
+    g = 0.9
+    d = penetration_depth(mua, musp)
+    scene = slab_scene(mua, musp / (1.0 - g), g, 1.38, 40.0 * d, half=50.0)
+    return Workload(f"jacques_slab_{wavelength_nm}nm", scene,
+                    Source(SQUARE, (0.0, 0.0, 0.05), (0.0, 0.0, -1.0), 2.0),
+                    Grid((-1.0, -1.0, -16.0 * d), (1.0, 1.0, 0.0), grid_n), npackets, seed, precision)
+
+
+def iso_sphere(tau: float = 100.0, npackets: int = 1_000_000, seed: int = 7, precision: str = "mixed",
+               grid_n: int = 200) -> Workload:
+    """Photons released isotropically from the centre of a pure isotropic
+    scatterer of radius 0.5 cm and radial optical depth tau (Sec. 3.1, Eq. 4;
+    at tau = 100 with 1e6 photons and a 200^3 grid, the timing case of
+    Table 2)."""
+    return Workload(f"iso_sphere_tau{tau:g}", isotropic_sphere(tau, 0.5),
+                    Source(ISO_POINT, (0.0, 0.0, 0.0), (0.0, 0.0, -1.0)),
+                    Grid((-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), (grid_n, grid_n, grid_n)),
+                    npackets, seed, precision)
+
+
 def all_configs():
     """The four single-job workloads at their stated sizes."""
     return [sphere_pencil(), three_layer_slab(), vessel_network(), glass_container()]
