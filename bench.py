@@ -302,7 +302,7 @@ def paper_cases(ctx, smc, stream, stepping: str):
             psi = phi / FX / (area * dz) / (n / (2 * wl.source.radius) ** 2)
             e["psi_over_incident_at_z"] = {f"{m}delta": float(np.interp(m * d, z, psi)) for m in (1, 2, 4)}
         else:
-            tau = wl.scene.regions[0].mu_s * wl.scene.prims[0].p[3]
+            tau = wl.scene.regions[0].mu_s * wl.scene.prims[0].params[3]
             want = tau * tau / 2 + tau
             e["eq4"] = {"mean_scatterings": t["scatters"] / n, "eq4": want,
                         "rel_diff": (t["scatters"] / n - want) / want}

@@ -74,7 +74,7 @@ EQ4_ROWS = [tuple(float(x) for x in r) for r in read_golden("eq4_scatterings.txt
 def test_eq4_mean_scatterings_gpu(ctx, tau, radius, tol, stepping):
     n = 100_000 if tau >= 100 else 400_000
     wl = W.iso_sphere(tau, n, grid_n=1).with_stepping(stepping)
-    assert wl.scene.prims[0].p[3] == radius
+    assert wl.scene.prims[0].params[3] == radius
     _, t = run_gpu(ctx, wl, "mixed", fluence=False)
     assert t["packets"] == n and t["max_steps_hit"] == 0
     mean = t["scatters"] / n
