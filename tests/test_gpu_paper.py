@@ -103,6 +103,16 @@ def test_table1_penetration_depth_gpu(ctx, row):
     # same bound as the oracle's pin: diffusion theory is approximate, and
     # using mu_s instead of mu_s (1 - g) would change k1 threefold
     assert abs(-slope * d - k1) < 0.08, (wavelength, -slope * d)
+    # absolute level against Eq. 5 with Table 1's coefficients: fluence over
+    # the grid's 2 x 2 cm per unit incident irradiance of the 4 x 4 cm source
+    C1, C2, k2 = float(row[3]), float(row[5]), float(row[6])
+    g = wl.grid
+    area = (g.hi[0] - g.lo[0]) * (g.hi[1] - g.lo[1])
+    psi = phi / FX / (area * 16.0 * d / nz) / (wl.npackets / (2 * wl.source.radius) ** 2)
+    for m in (1, 2, 4):
+        want = C1 * math.exp(-k1 * m) - C2 * math.exp(-k2 * m)
+        got = float(np.interp(m * d, z, psi))
+        assert abs(got - want) / want < 0.06, (wavelength, m, got, want)
     # energy closes: R + T + A + killed - gain = packets
     bal = (t["R"] + t["T"] + t["A"] + t["killed"] - t["gain"]) / FX
     assert abs(bal - wl.npackets) < 1e-4 * wl.npackets

@@ -564,6 +564,17 @@ def test_table1_penetration_depth(row):
     sel = (z > 4 * dpaper) & (z < 12 * dpaper)
     slope = np.polyfit(z[sel], np.log(phi[sel]), 1)[0]
     assert abs(-slope * dpaper - k1) < 0.08
+    # absolute level: the laterally integrated fluence of a pencil beam per
+    # incident photon equals the fluence rate under uniform illumination per
+    # unit irradiance, Psi / Psi0 of Eq. 5 with Table 1's C1, k1, C2, k2.
+    # The paper notes that bin shapes keep codes from matching exactly; 6 %.
+    C1, C2, k2 = float(row[3]), float(row[5]), float(row[6])
+    dz = thick / nz
+    psi = phi / FX / dz / tot["packets"]
+    for m in (1, 2, 4):
+        want = C1 * math.exp(-k1 * m) - C2 * math.exp(-k2 * m)
+        got = float(np.interp(m * dpaper, z, psi))
+        assert abs(got - want) / want < 0.06, (m, got, want)
 
 
 # --------------------------------------------------------------------------
