@@ -57,8 +57,42 @@ extern "C" {
 enum smcrt_prim_kind {
     SMCRT_SPHERE = 0,   /* p = {cx, cy, cz, r}: |x - c| - r (Eq. 2-3) */
     SMCRT_BOX = 1,      /* p = {cx, cy, cz, hx, hy, hz}: exact box distance */
-    SMCRT_CAPSULE = 2   /* p = {ax, ay, az, bx, by, bz, r}: segment distance - r */
+    SMCRT_CAPSULE = 2,  /* p = {ax, ay, az, bx, by, bz, r}: segment distance - r */
+    SMCRT_TORUS = 3,    /* p = {cx, cy, cz, R, r}, 0 < r < R: ring about the z axis
+                         * through c; distance to the core circle - r (Fig. 1 basic shapes) */
+    SMCRT_CYLINDER = 4  /* p = {cx, cy, cz, r, h}: capped cylinder along z through c,
+                         * radius r, half height h; exact distance */
 };
+
+/* Domain operation applied to a primitive's local coordinates (Sec. 2.2:
+ * SDFs "can easily be translated, rotated, twisted and scaled"; Fig. 1
+ * i, o, p, q).  Operations that stretch space divide the distance by their
+ * Lipschitz bound, so it never exceeds the true distance (Sec. 5 on
+ * non-bounded SDFs). */
+enum smcrt_domain_op {
+    SMCRT_XF_NONE = 0,
+    SMCRT_XF_ELONGATE = 1,  /* a[0..2] >= 0: q - clamp(q, -a, a) (exact outside) */
+    SMCRT_XF_TWIST = 2,     /* (x, y) rotated by 2 pi a[0] z (a[0] turns per unit length);
+                             * a[1] >= 0 the radius the shape reaches from the axis.  With
+                             * m = 2 pi a[0] max(rho, a[1]) the distance is divided by
+                             * (m + sqrt(m^2 + 4)) / 2, the map's largest stretch */
+    SMCRT_XF_BEND = 3,      /* (x, y) rotated by 2 pi a[0] x; a[1] as for twist; divided
+                             * by 1 + m */
+    SMCRT_XF_REPEAT = 4     /* a[0..2] >= 0 periods (0 = not repeated), a[3] >= 0 integer
+                             * copies each way: nearest copy; exact for a shape centred
+                             * at the local origin and inside its cell */
+};
+
+/* Frame of a primitive: the point with local coordinates l sits at
+ * s R l + t.  The distance is s * d_local(op(R^T (x - t) / s)) / L. */
+typedef struct {
+    double rot[9];      /* R, row-major, orthonormal with det +1 (1e-9) */
+    double t[3];        /* translation (cm) */
+    double s;           /* uniform scale, > 0 */
+    int32_t op;         /* enum smcrt_domain_op */
+    int32_t reserved;   /* must be 0 */
+    double a[4];        /* parameters of op */
+} smcrt_xform;
 
 enum smcrt_op {         /* postfix CSG program nodes (Sec. 2.2, Fig. 1 e-h) */
     SMCRT_OP_PRIM = 0,          /* push primitive `prim` */
@@ -70,7 +104,7 @@ enum smcrt_op {         /* postfix CSG program nodes (Sec. 2.2, Fig. 1 e-h) */
 
 typedef struct {
     int32_t kind;       /* enum smcrt_prim_kind */
-    int32_t reserved;   /* must be 0 */
+    int32_t xform;      /* 0: p in scene coordinates; k > 0: p in the frame xforms[k - 1] */
     double p[7];        /* parameters, see smcrt_prim_kind */
 } smcrt_prim;
 
@@ -126,6 +160,9 @@ typedef struct {
     int64_t max_steps;             /* per-packet step cap (grazing guard), > 0 */
     int32_t stepping;              /* enum smcrt_stepping */
     int32_t reserved;              /* must be 0 */
+    const smcrt_xform *xforms;     /* host array of nxforms (may be NULL if 0) */
+    int32_t nxforms;               /* 0 .. 4096 */
+    int32_t reserved2;             /* must be 0 */
 } smcrt_scene;
 
 enum smcrt_source_kind {

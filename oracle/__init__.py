@@ -34,7 +34,12 @@ FX = 2.0 ** 32  # fixed-point scale of every tally
 
 
 class OrPrim(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("p", C.c_double * 7)]
+    _fields_ = [("kind", C.c_int32), ("xform", C.c_int32), ("p", C.c_double * 7)]
+
+
+class OrXform(C.Structure):
+    _fields_ = [("rot", C.c_double * 9), ("t", C.c_double * 3), ("s", C.c_double), ("op", C.c_int32),
+                ("pad", C.c_int32), ("a", C.c_double * 4)]
 
 
 class OrNode(C.Structure):
@@ -52,7 +57,8 @@ class OrScene(C.Structure):
                 ("regions", C.POINTER(OrRegion)), ("nregions", C.c_int32),
                 ("ambient_n", C.c_double), ("bbox_lo", C.c_double * 3),
                 ("bbox_hi", C.c_double * 3), ("delta", C.c_double), ("max_steps", C.c_int64),
-                ("stepping", C.c_int32), ("pad", C.c_int32)]
+                ("stepping", C.c_int32), ("pad", C.c_int32),
+                ("xforms", C.POINTER(OrXform)), ("nxforms", C.c_int32), ("pad2", C.c_int32)]
 
 
 class OrSource(C.Structure):
@@ -76,7 +82,8 @@ class OrTotals(C.Structure):
 PACKET_FIELDS = ["R", "T", "A", "killed", "gain", "scatters", "steps", "pad"]
 PACKET_DTYPE = np.dtype([(f, np.int64) for f in PACKET_FIELDS])
 
-_PRIM_KIND = {W.SPHERE: 0, W.BOX: 1, W.CAPSULE: 2}
+_PRIM_KIND = {W.SPHERE: 0, W.BOX: 1, W.CAPSULE: 2, W.TORUS: 3, W.CYLINDER: 4}
+_XF_OP = {W.XF_NONE: 0, W.ELONGATE: 1, W.TWIST: 2, W.BEND: 3, W.REPEAT: 4}
 _OP = {W.PRIM: 0, W.UNION: 1, W.SMOOTH_UNION: 2, W.INTERSECT: 3, W.SUBTRACT: 4}
 _SRC_KIND = {W.PENCIL: 0, W.DISC: 1, W.SQUARE: 2, W.ISO_POINT: 3}
 _STEPPING = {W.SPHERE_TRACING: 0, W.SEGMENT: 1}
@@ -143,6 +150,7 @@ def lib():
             for i, s in enumerate([OrPrim, OrNode, OrRegion, OrScene, OrSource, OrGrid, OrTotals]):
                 assert L.or_sizeof(i) == C.sizeof(s), (i, L.or_sizeof(i), C.sizeof(s))
             assert L.or_sizeof(7) == PACKET_DTYPE.itemsize
+            assert L.or_sizeof(8) == C.sizeof(OrXform)
             _lib = L
     return _lib
 
@@ -152,10 +160,21 @@ class _SceneHolder:
 
     def __init__(self, scene: W.Scene):
         prims = (OrPrim * max(1, len(scene.prims)))()
+        xf_l = []
         for i, pr in enumerate(scene.prims):
             prims[i].kind = _PRIM_KIND[pr.kind]
             for j, v in enumerate(pr.params):
                 prims[i].p[j] = float(v)
+            if pr.xform is not None:
+                xf_l.append(pr.xform)
+                prims[i].xform = len(xf_l)
+        xforms = (OrXform * max(1, len(xf_l)))()
+        for i, X in enumerate(xf_l):
+            xforms[i].rot[:] = [float(v) for v in X.rot]
+            xforms[i].t[:] = [float(v) for v in X.t]
+            xforms[i].s, xforms[i].op = float(X.s), _XF_OP[X.op]
+            xforms[i].a[:] = [float(v) for v in X.a]
+        self.xforms = xforms
         nodes_l, regs = [], (OrRegion * max(1, len(scene.regions)))()
         for r, reg in enumerate(scene.regions):
             regs[r].begin = len(nodes_l)
@@ -169,7 +188,7 @@ class _SceneHolder:
         self.s = OrScene(prims, len(scene.prims), nodes, len(nodes_l), regs, len(scene.regions),
                          float(scene.ambient_n), (C.c_double * 3)(*scene.bbox_lo),
                          (C.c_double * 3)(*scene.bbox_hi), float(scene.delta), int(scene.max_steps),
-                         _STEPPING[scene.stepping], 0)
+                         _STEPPING[scene.stepping], 0, xforms, len(xf_l), 0)
 
 
 def _source(src: W.Source) -> OrSource:

@@ -44,7 +44,17 @@
 /* ------------------------------------------------------------------------
  * Private structures (not shared with the CUDA side).
  * ---------------------------------------------------------------------- */
-typedef struct { int32_t kind; int32_t pad; double p[7]; } or_prim;     /* 0 sphere, 1 box, 2 capsule */
+/* kind: 0 sphere, 1 box, 2 capsule, 3 torus, 4 capped cylinder; xform: 0 none,
+ * k > 0 the primitive sits in frame xforms[k - 1] */
+typedef struct { int32_t kind; int32_t xform; double p[7]; } or_prim;
+/* Placement and domain operation of a primitive (Sec. 2.2: SDFs can be
+ * translated, rotated, scaled, twisted, bent, elongated, repeated).  A point
+ * with local coordinates l sits at s R l + t (R row-major, orthonormal).
+ * op on the local point: 0 none, 1 elongate (a[0..2] half lengths),
+ * 2 twist about local z (a[0] turns per unit length, a[1] radius reached by
+ * the shape), 3 bend in the local x-y plane (same parameters, angle from x),
+ * 4 repeat (a[0..2] periods, 0 = not repeated; a[3] copies each way). */
+typedef struct { double rot[9], t[3], s; int32_t op, pad; double a[4]; } or_xform;
 typedef struct { int32_t op; int32_t prim; double k; } or_node;         /* 0 prim,1 union,2 smooth,3 inter,4 sub */
 typedef struct { int32_t begin, count; double mu_a, mu_s, g, n; } or_region;
 typedef struct {
@@ -57,6 +67,8 @@ typedef struct {
     int64_t max_steps;
     int32_t stepping;          /* 0 sphere tracing (Sec. 2.3), 1 segment stepping (below) */
     int32_t pad;
+    const or_xform *xforms; int32_t nxforms;
+    int32_t pad2;
 } or_scene;
 typedef struct { int32_t kind; int32_t pad; double pos[3], dir[3], radius; } or_source; /* 0 pencil,1 disc,2 square,3 iso */
 typedef struct { double lo[3], hi[3]; int32_t n[3]; int32_t pad; } or_grid;
@@ -201,11 +213,81 @@ static double sdf_capsule(const double p[3], const double *q)
     return sqrt(dx * dx + dy * dy + dz * dz) - q[6];
 }
 
-static double sdf_prim(const or_prim *pr, const double p[3])
+static double sdf_torus(const double p[3], const double *q)
+{   /* ring of major radius R = q[3] about the z axis through c, tube radius
+     * r = q[4]: distance to the core circle minus r */
+    double dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+    double ring = sqrt(dx * dx + dy * dy) - q[3];
+    return sqrt(ring * ring + dz * dz) - q[4];
+}
+
+static double sdf_cylinder(const double p[3], const double *q)
+{   /* capped cylinder along z through c, radius q[3], half height q[4]:
+     * the exact distance of a 2D box in (radial, axial) coordinates */
+    double dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+    double a = sqrt(dx * dx + dy * dy) - q[3];
+    double b = fabs(dz) - q[4];
+    double ma = fmax(a, 0.0), mb = fmax(b, 0.0);
+    return fmin(fmax(a, b), 0.0) + sqrt(ma * ma + mb * mb);
+}
+
+static double sdf_base(int kind, const double *q, const double p[3])
 {
-    if (pr->kind == 0) return sdf_sphere(p, pr->p);
-    if (pr->kind == 1) return sdf_box(p, pr->p, pr->p + 3);
-    return sdf_capsule(p, pr->p);
+    if (kind == 0) return sdf_sphere(p, q);
+    if (kind == 1) return sdf_box(p, q, q + 3);
+    if (kind == 2) return sdf_capsule(p, q);
+    if (kind == 3) return sdf_torus(p, q);
+    return sdf_cylinder(p, q);
+}
+
+/* A primitive in its frame: map p to local coordinates (inverse placement),
+ * apply the domain operation, evaluate, scale back by s and divide by the
+ * operation's Lipschitz bound L, so the value never exceeds the true
+ * distance and sphere tracing stays safe (the paper's caution about
+ * non-bounded SDFs, Sec. 5). */
+static double sdf_xprim(const or_prim *pr, const or_xform *X, const double p[3])
+{
+    double vx = p[0] - X->t[0], vy = p[1] - X->t[1], vz = p[2] - X->t[2];
+    double q[3];
+    q[0] = (X->rot[0] * vx + X->rot[3] * vy + X->rot[6] * vz) / X->s;
+    q[1] = (X->rot[1] * vx + X->rot[4] * vy + X->rot[7] * vz) / X->s;
+    q[2] = (X->rot[2] * vx + X->rot[5] * vy + X->rot[8] * vz) / X->s;
+    double L = 1.0;
+    if (X->op == 1) {                        /* elongate: stretch the centre */
+        for (int a = 0; a < 3; ++a) q[a] = q[a] - fmin(fmax(q[a], -X->a[a]), X->a[a]);
+    } else if (X->op == 2 || X->op == 3) {   /* twist about z / bend about the x-y plane */
+        double rho = sqrt(q[0] * q[0] + q[1] * q[1]);
+        double sn, cs;
+        or_sincos2pi(X->a[0] * (X->op == 2 ? q[2] : q[0]), &sn, &cs);
+        double x = cs * q[0] - sn * q[1];
+        double y = sn * q[0] + cs * q[1];
+        q[0] = x; q[1] = y;
+        /* largest stretch of the map within radius rho of the axis, with
+         * m = 2 pi a0 rho: its Jacobian is a rotation times I + m N, N of
+         * norm one; for the twist the largest singular value of
+         * [[I, m e], [0, 1]] is (m + sqrt(m^2 + 4)) / 2, for the bend that
+         * of I + m N is 1 + m.  rho: the larger of the point's and the
+         * shape's radius, so the bound holds on the whole segment from the
+         * point to the surface (rho is convex along it). */
+        double m = 6.283185307179586 * X->a[0] * fmax(rho, X->a[1]);
+        L = X->op == 2 ? 0.5 * (m + sqrt(m * m + 4.0)) : 1.0 + m;
+    } else if (X->op == 4) {                 /* repetition: nearest copy, at most a[3] each way */
+        for (int a = 0; a < 3; ++a) {
+            double c = X->a[a];
+            if (c > 0.0) {
+                double k = floor(q[a] / c + 0.5);
+                k = fmin(fmax(k, -X->a[3]), X->a[3]);
+                q[a] = q[a] - c * k;
+            }
+        }
+    }
+    return X->s * sdf_base(pr->kind, pr->p, q) / L;
+}
+
+static double sdf_prim(const or_scene *S, const or_prim *pr, const double p[3])
+{
+    if (pr->xform > 0) return sdf_xprim(pr, &S->xforms[pr->xform - 1], p);
+    return sdf_base(pr->kind, pr->p, p);
 }
 
 /* CSG on two distances: a is the left (earlier) operand, b the right. */
@@ -231,7 +313,7 @@ static double region_sdf(const or_scene *S, int r, const double p[3], or_totals 
     for (int i = 0; i < R->count; ++i) {
         const or_node *nd = &S->nodes[R->begin + i];
         if (nd->op == 0) {
-            st[sp++] = sdf_prim(&S->prims[nd->prim], p);
+            st[sp++] = sdf_prim(S, &S->prims[nd->prim], p);
             if (T) T->prim_evals += 1;
         } else {
             double b = st[--sp];
@@ -611,13 +693,14 @@ static double segment_box(const double c[3], const double h[3], double d, const 
     return tf > 0.0 ? tf : 0.0;          /* inside: exit of the shrunk box */
 }
 
-static double segment_prim(const or_prim *pr, const double p[3], const double u[3], double dh)
+static double segment_prim(const or_scene *S, const or_prim *pr, const double p[3], const double u[3],
+                           double dh)
 {
-    double d = sdf_prim(pr, p);
+    double d = sdf_prim(S, pr, p);
     if (!(fabs(d) > dh)) return 0.0;
-    if (pr->kind == 0) return segment_sphere(pr->p, d, p, u, dh);
-    if (pr->kind == 1) return segment_box(pr->p, pr->p + 3, d, p, u, dh);
-    return fabs(d) - dh;                 /* capsule: isotropic bound */
+    if (pr->xform == 0 && pr->kind == 0) return segment_sphere(pr->p, d, p, u, dh);
+    if (pr->xform == 0 && pr->kind == 1) return segment_box(pr->p, pr->p + 3, d, p, u, dh);
+    return fabs(d) - dh;                 /* other shapes and placed ones: isotropic bound */
 }
 
 /* Largest safe move from p along u (scene evaluated at p in E). */
@@ -630,7 +713,7 @@ static double segment_bound(const or_scene *S, const or_eval *E, const double p[
         const or_region *R = &S->regions[r];
         for (int i = 0; i < R->count; ++i) {
             const or_node *nd = &S->nodes[R->begin + i];
-            if (nd->op == 0) t = fmin(t, segment_prim(&S->prims[nd->prim], p, u, dh));
+            if (nd->op == 0) t = fmin(t, segment_prim(S, &S->prims[nd->prim], p, u, dh));
         }
     }
     double c[3], h[3];
@@ -733,6 +816,12 @@ int or_run(const or_scene *S, const or_source *src, const or_grid *G, uint64_t i
 {
     if (!S || !src || !G || !tot) return -1;
     if (!(S->delta > 0.0) || S->nregions < 0 || S->stepping < 0 || S->stepping > 1) return -2;
+    for (int i = 0; i < S->nprims; ++i) {
+        if (S->prims[i].kind < 0 || S->prims[i].kind > 4) return -8;
+        if (S->prims[i].xform < 0 || S->prims[i].xform > S->nxforms) return -9;
+    }
+    for (int i = 0; i < S->nxforms; ++i)
+        if (!(S->xforms[i].s > 0.0) || S->xforms[i].op < 0 || S->xforms[i].op > 4) return -10;
     for (int r = 0; r < S->nregions; ++r) {     /* postfix stack check */
         int sp = 0;
         const or_region *R = &S->regions[r];
@@ -820,6 +909,7 @@ int or_sizeof(int which)
     case 5: return (int)sizeof(or_grid);
     case 6: return (int)sizeof(or_totals);
     case 7: return (int)sizeof(or_packet);
+    case 8: return (int)sizeof(or_xform);
     default: return -1;
     }
 }

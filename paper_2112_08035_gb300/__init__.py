@@ -27,7 +27,8 @@ OK, ERR_BAD_ARG, ERR_BAD_SCENE, ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_CANCEL
 FP64, MIXED = 0, 1
 FX = 2.0 ** 32
 
-_PRIM_KIND = {"sphere": 0, "box": 1, "capsule": 2}
+_PRIM_KIND = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "cylinder": 4}
+_XF_OP = {"none": 0, "elongate": 1, "twist": 2, "bend": 3, "repeat": 4}
 _OP = {"prim": 0, "union": 1, "smooth_union": 2, "intersect": 3, "subtract": 4}
 _SRC_KIND = {"pencil": 0, "disc": 1, "square": 2, "iso": 3}
 _STEPPING = {"sphere_tracing": 0, "segment": 1}
@@ -35,7 +36,12 @@ _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
 
 class Prim(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("p", C.c_double * 7)]
+    _fields_ = [("kind", C.c_int32), ("xform", C.c_int32), ("p", C.c_double * 7)]
+
+
+class Xform(C.Structure):
+    _fields_ = [("rot", C.c_double * 9), ("t", C.c_double * 3), ("s", C.c_double), ("op", C.c_int32),
+                ("reserved", C.c_int32), ("a", C.c_double * 4)]
 
 
 class CsgNode(C.Structure):
@@ -53,7 +59,8 @@ class Scene(C.Structure):
                 ("regions", C.POINTER(Region)), ("nregions", C.c_int32),
                 ("ambient_n", C.c_double), ("bbox_lo", C.c_double * 3), ("bbox_hi", C.c_double * 3),
                 ("delta", C.c_double), ("max_steps", C.c_int64), ("stepping", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("xforms", C.POINTER(Xform)), ("nxforms", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 class Source(C.Structure):
@@ -154,10 +161,20 @@ class Marshalled:
     def __init__(self, scene, source, grid):
         np_ = len(scene.prims)
         self.prims = (Prim * np_)()
+        xf = []
         for i, pr in enumerate(scene.prims):
             self.prims[i].kind = _PRIM_KIND[pr.kind]
             for j, v in enumerate(pr.params):
                 self.prims[i].p[j] = float(v)
+            if getattr(pr, "xform", None) is not None:
+                xf.append(pr.xform)
+                self.prims[i].xform = len(xf)
+        self.xforms = (Xform * max(1, len(xf)))()
+        for i, X in enumerate(xf):
+            self.xforms[i].rot[:] = [float(v) for v in X.rot]
+            self.xforms[i].t[:] = [float(v) for v in X.t]
+            self.xforms[i].s, self.xforms[i].op = float(X.s), _XF_OP[X.op]
+            self.xforms[i].a[:] = [float(v) for v in X.a]
         nodes, regs = [], (Region * len(scene.regions))()
         for r, reg in enumerate(scene.regions):
             regs[r].node_begin, regs[r].node_count = len(nodes), len(reg.program)
@@ -170,7 +187,7 @@ class Marshalled:
         self.scene = Scene(self.prims, np_, self.nodes, len(nodes), regs, len(scene.regions),
                            float(scene.ambient_n), (C.c_double * 3)(*scene.bbox_lo),
                            (C.c_double * 3)(*scene.bbox_hi), float(scene.delta), int(scene.max_steps),
-                           _STEPPING[scene.stepping], 0)
+                           _STEPPING[scene.stepping], 0, self.xforms, len(xf), 0)
         self.source = Source(_SRC_KIND[source.kind], 0, (C.c_double * 3)(*source.pos),
                              (C.c_double * 3)(*source.dir), float(source.radius))
         self.grid = Grid((C.c_double * 3)(*grid.lo), (C.c_double * 3)(*grid.hi),

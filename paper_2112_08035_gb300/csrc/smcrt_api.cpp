@@ -81,9 +81,38 @@ int validate(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid *g
         } else if (p.kind == SMCRT_CAPSULE) {
             const double dx = p.p[3] - p.p[0], dy = p.p[4] - p.p[1], dz = p.p[5] - p.p[2];
             if (!(p.p[6] > 0) || !(dx * dx + dy * dy + dz * dz > 0)) return SMCRT_ERR_BAD_SCENE;
+        } else if (p.kind == SMCRT_TORUS) {
+            if (!(p.p[4] > 0 && p.p[3] > p.p[4])) return SMCRT_ERR_BAD_SCENE;
+        } else if (p.kind == SMCRT_CYLINDER) {
+            if (!(p.p[3] > 0 && p.p[4] > 0)) return SMCRT_ERR_BAD_SCENE;
         } else {
             return SMCRT_ERR_BAD_SCENE;
         }
+        if (p.xform < 0 || p.xform > sc->nxforms) return SMCRT_ERR_BAD_SCENE;
+    }
+    if (sc->nxforms < 0 || sc->nxforms > kMaxPrims || (sc->nxforms > 0 && !sc->xforms)) return SMCRT_ERR_BAD_SCENE;
+    for (int i = 0; i < sc->nxforms; ++i) {
+        const smcrt_xform &X = sc->xforms[i];
+        bool ok = finite(X.s) && X.s > 0 && X.op >= SMCRT_XF_NONE && X.op <= SMCRT_XF_REPEAT;
+        for (int k = 0; k < 9; ++k) ok = ok && finite(X.rot[k]);
+        for (int k = 0; k < 3; ++k) ok = ok && finite(X.t[k]);
+        for (int k = 0; k < 4; ++k) ok = ok && finite(X.a[k]);
+        if (!ok) return SMCRT_ERR_BAD_SCENE;
+        for (int a = 0; a < 3; ++a)          // orthonormal columns
+            for (int b = 0; b < 3; ++b) {
+                const double dot = X.rot[a] * X.rot[b] + X.rot[3 + a] * X.rot[3 + b] + X.rot[6 + a] * X.rot[6 + b];
+                if (!(std::fabs(dot - (a == b ? 1.0 : 0.0)) < 1e-9)) return SMCRT_ERR_BAD_SCENE;
+            }
+        const double *R = X.rot;
+        const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                           R[2] * (R[3] * R[7] - R[4] * R[6]);
+        if (!(det > 0)) return SMCRT_ERR_BAD_SCENE;
+        if (X.op == SMCRT_XF_ELONGATE && !(X.a[0] >= 0 && X.a[1] >= 0 && X.a[2] >= 0)) return SMCRT_ERR_BAD_SCENE;
+        if ((X.op == SMCRT_XF_TWIST || X.op == SMCRT_XF_BEND) && !(X.a[1] >= 0)) return SMCRT_ERR_BAD_SCENE;
+        if (X.op == SMCRT_XF_REPEAT &&
+            !(X.a[0] >= 0 && X.a[1] >= 0 && X.a[2] >= 0 && X.a[3] >= 0 && X.a[3] <= 1e6 &&
+              X.a[3] == std::floor(X.a[3])))
+            return SMCRT_ERR_BAD_SCENE;
     }
     for (int r = 0; r < sc->nregions; ++r) {
         const smcrt_region &R = sc->regions[r];
@@ -128,7 +157,7 @@ int compile(const smcrt_scene *sc, std::vector<Instr> &ins, std::vector<double> 
             if (op == SMCRT_OP_PRIM) {
                 const int p = nd[i].prim;
                 if (p < 0 || p >= sc->nprims) return SMCRT_ERR_BAD_SCENE;
-                const int kind = sc->prims[p].kind;
+                const int kind = device_kind(sc->prims[p]);
                 const bool fuse = depth >= 1 && i + 1 < R.node_count && nd[i + 1].op >= SMCRT_OP_UNION &&
                                   nd[i + 1].op <= SMCRT_OP_SUBTRACT;
                 Instr in{};
@@ -235,6 +264,10 @@ struct smcrt_plan {
 
 namespace {
 
+// Kernel instantiation of a plan: its register variant, in the general-shape
+// family when the scene has tori, cylinders or primitive frames.
+int kvariant(const smcrt_plan *pl) { return pl->variant + (pl->host.general ? kNumVariants : 0); }
+
 int occupancy(int precision, int threads, int variant)
 {
     return precision == SMCRT_FP64 ? occupancy_fp64(threads, variant) : occupancy_mixed(threads, variant);
@@ -257,6 +290,7 @@ uint64_t shape_key(const smcrt_scene *sc, int precision, const smcrt_grid *g)
     auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
     mix((uint64_t)precision);
     mix((uint64_t)sc->stepping);
+    mix((uint64_t)sc->nxforms);
     mix((uint64_t)sc->nprims);
     mix((uint64_t)sc->nregions);
     mix((uint64_t)sc->nnodes);
@@ -272,6 +306,7 @@ bool fold_region(const smcrt_scene *sc, int r, int *op, double *k, std::vector<i
     const smcrt_region &R = sc->regions[r];
     const smcrt_csg_node *nd = sc->nodes + R.node_begin;
     if (R.node_count < 3 || (R.node_count - 1) % 2 != 0 || nd[0].op != SMCRT_OP_PRIM) return false;
+    if (nd[0].prim < 0 || nd[0].prim >= sc->nprims || !plain_prim(sc->prims[nd[0].prim])) return false;
     prims->clear();
     prims->push_back(nd[0].prim);
     int o = -1;
@@ -279,6 +314,8 @@ bool fold_region(const smcrt_scene *sc, int r, int *op, double *k, std::vector<i
     for (int i = 1; i + 1 < R.node_count; i += 2) {
         const int bop = nd[i + 1].op;
         if (nd[i].op != SMCRT_OP_PRIM || (bop != SMCRT_OP_UNION && bop != SMCRT_OP_SMOOTH_UNION)) return false;
+        if (nd[i].prim < 0 || nd[i].prim >= sc->nprims || !plain_prim(sc->prims[nd[i].prim]))
+            return false;   // the grid bounds spheres, boxes, capsules
         if (o < 0) {
             o = bop;
             kk = bop == SMCRT_OP_SMOOTH_UNION ? nd[i + 1].k : 0.0;
@@ -393,25 +430,13 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     std::vector<int32_t> pkind(np);
     std::vector<double> p64((size_t)np * 8, 0.0);
     std::vector<float4> p32((size_t)np * 2, make_float4(0, 0, 0, 0));
+    const bool has_xf = sc->nxforms > 0;
+    std::vector<double> xf64(has_xf ? (size_t)np * kXf64 : 0);
+    std::vector<float4> xf32(has_xf ? (size_t)np * kXf32 : 0);
     for (int i = 0; i < np; ++i) {
-        const smcrt_prim &P = sc->prims[i];
-        pkind[i] = P.kind;
-        double *d = &p64[(size_t)8 * i];
-        if (P.kind == SMCRT_CAPSULE) {
-            const double bax = P.p[3] - P.p[0], bay = P.p[4] - P.p[1], baz = P.p[5] - P.p[2];
-            const double baba = bax * bax + bay * bay + baz * baz;
-            d[0] = P.p[0]; d[1] = P.p[1]; d[2] = P.p[2];
-            d[3] = bax; d[4] = bay; d[5] = baz; d[6] = P.p[6]; d[7] = baba;
-            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[6]);
-            p32[2 * i + 1] = make_float4((float)bax, (float)bay, (float)baz, (float)(1.0 / baba));
-        } else if (P.kind == SMCRT_BOX) {
-            for (int k = 0; k < 6; ++k) d[k] = P.p[k];
-            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], 0.f);
-            p32[2 * i + 1] = make_float4((float)P.p[3], (float)P.p[4], (float)P.p[5], 0.f);
-        } else {
-            for (int k = 0; k < 4; ++k) d[k] = P.p[k];
-            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[3]);
-        }
+        pkind[i] = device_kind(sc->prims[i]);
+        fill_prim(sc, i, &p64[(size_t)8 * i], &p32[(size_t)2 * i], has_xf ? &xf64[(size_t)kXf64 * i] : nullptr,
+                  has_xf ? &xf32[(size_t)kXf32 * i] : nullptr);
     }
     std::vector<double> reg64((size_t)nr * 8, 0.0);
     std::vector<float4> reg32((size_t)nr * 2);
@@ -444,6 +469,8 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     std::vector<int32_t> segp(sc->stepping == SMCRT_STEP_SEGMENT ? kMaxPrims : 0);
     const int nseg = segp.empty() ? 0 : hard_region_prims(sc, segp.data());
     const size_t o_seg = take(sizeof(int32_t) * nseg);
+    const size_t o_xf64 = take(sizeof(double) * xf64.size());
+    const size_t o_xf32 = take(sizeof(float4) * xf32.size());
     const size_t total = off;
 
     std::unique_ptr<smcrt_plan> pl(new smcrt_plan());
@@ -498,10 +525,16 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     H.stepping = sc->stepping;
     H.nseg = nseg;
     H.seg_prims = nseg > 0 ? (const int32_t *)(base + o_seg) : nullptr;
-    {   // analytic normals when every region's program is short
+    H.xf64 = has_xf ? (const double *)(base + o_xf64) : nullptr;
+    H.xf32 = has_xf ? (const float4 *)(base + o_xf32) : nullptr;
+    for (int i = 0; i < np; ++i) H.general = H.general || !plain_prim(sc->prims[i]);
+    {   // analytic normals when every region's program is short and made of
+        // spheres, boxes and capsules in scene coordinates
         int longest = 0;
+        bool plain = true;
         for (int r = 0; r < nr; ++r) longest = std::max(longest, rr[r].y - rr[r].x);
-        H.analytic_nrm = longest <= kAnalyticNormalMaxInstr ? 1 : 0;
+        for (int i = 0; i < np; ++i) plain = plain && plain_prim(sc->prims[i]);
+        H.analytic_nrm = longest <= kAnalyticNormalMaxInstr && plain ? 1 : 0;
     }
     H.delta32 = std::max((float)sc->delta, 64.f * ulp_f32(rmax));
     H.h32 = 32.f * H.delta32;
@@ -540,6 +573,10 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     if (!cg.off.empty()) std::memcpy(hb.data() + o_coff, cg.off.data(), sizeof(int32_t) * cg.off.size());
     if (!cg.list.empty()) std::memcpy(hb.data() + o_clist, cg.list.data(), sizeof(int32_t) * cg.list.size());
     if (nseg > 0) std::memcpy(hb.data() + o_seg, segp.data(), sizeof(int32_t) * nseg);
+    if (has_xf) {
+        std::memcpy(hb.data() + o_xf64, xf64.data(), sizeof(double) * xf64.size());
+        std::memcpy(hb.data() + o_xf32, xf32.data(), sizeof(float4) * xf32.size());
+    }
     pl->dscene = (DevScene *)(base + o_scene);
     pl->cells = (size_t)g->n[0] * g->n[1] * g->n[2];
     if (serving_stream) {
@@ -584,7 +621,7 @@ void default_launch(const smcrt_plan *pl, int &blocks, int &threads)
     threads = pl->threads > 0 ? pl->threads : 128;
     blocks = pl->blocks;
     if (blocks <= 0) {
-        const int occ = std::max(1, occupancy(pl->precision, threads, pl->variant));
+        const int occ = std::max(1, occupancy(pl->precision, threads, kvariant(pl)));
         blocks = pl->ctx->sm_count * occ;
     }
 }
@@ -605,7 +642,7 @@ int plan_launch_impl(smcrt_plan *pl, uint64_t id_begin, uint64_t n, uint64_t see
     JobWork *slot = pl->djobs + pl->ring_pos;
     pl->ring_pos = (pl->ring_pos + 1) % pl->ring;
     if (launch_set_job(slot, jw, s) != cudaSuccess) return SMCRT_ERR_CUDA;
-    if (launch_kernel(pl->precision, slot, 1, pl->dstatus, blocks, threads, s, pl->variant) != cudaSuccess)
+    if (launch_kernel(pl->precision, slot, 1, pl->dstatus, blocks, threads, s, kvariant(pl)) != cudaSuccess)
         return SMCRT_ERR_CUDA;
     return SMCRT_OK;
 }
@@ -631,6 +668,7 @@ struct Job {
     std::vector<smcrt_prim> prims;
     std::vector<smcrt_csg_node> nodes;
     std::vector<smcrt_region> regions;
+    std::vector<smcrt_xform> xforms;
     smcrt_scene scene{};
     smcrt_source source{};
     smcrt_grid grid{};
@@ -737,7 +775,8 @@ void scheduler(smcrt_ctx *ctx)
     struct Buf {
         JobWork *h_tab = nullptr, *d_tab = nullptr;   // [2 * kMaxSlots]: mixed table, then FP64 table
         smcrt_totals *h_tot = nullptr;                // totals snapshot taken at the end of the round
-        cudaGraphExec_t graph = nullptr;
+        cudaGraphExec_t graph = nullptr;     // plain scenes only
+        cudaGraphExec_t graph_g = nullptr;   // kernels for scenes with general shapes
         cudaEvent_t ev = nullptr, ev0 = nullptr;
         bool busy = false;
         int64_t idx = -1;
@@ -753,20 +792,24 @@ void scheduler(smcrt_ctx *ctx)
         cudaEventCreate(&b.ev);
         cudaEventCreate(&b.ev0);
         std::memset(b.h_tab, 0, sizeof(JobWork) * 2 * kMaxSlots);
-        cudaGraph_t g;
-        cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-        cudaMemcpyAsync(b.d_tab, b.h_tab, sizeof(JobWork) * 2 * kMaxSlots, cudaMemcpyHostToDevice, st);
-        launch_round_prologue(b.d_tab, 2 * kMaxSlots, st);
-        cudaEventRecord(ev_fork, st);
-        cudaStreamWaitEvent(st2, ev_fork, 0);
-        launch_mixed(b.d_tab, kMaxSlots, d_status, blocks_m, threads, st, default_variant(SMCRT_MIXED));
-        launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status, blocks_d, threads, st2, default_variant(SMCRT_FP64));
-        cudaEventRecord(ev_join, st2);
-        cudaStreamWaitEvent(st, ev_join, 0);
-        cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
-        cudaStreamEndCapture(st, &g);
-        cudaGraphInstantiate(&b.graph, g, 0);
-        cudaGraphDestroy(g);
+        for (int gen = 0; gen < 2; ++gen) {
+            const int off = gen ? kNumVariants : 0;
+            cudaGraph_t g;
+            cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            cudaMemcpyAsync(b.d_tab, b.h_tab, sizeof(JobWork) * 2 * kMaxSlots, cudaMemcpyHostToDevice, st);
+            launch_round_prologue(b.d_tab, 2 * kMaxSlots, st);
+            cudaEventRecord(ev_fork, st);
+            cudaStreamWaitEvent(st2, ev_fork, 0);
+            launch_mixed(b.d_tab, kMaxSlots, d_status, blocks_m, threads, st, default_variant(SMCRT_MIXED) + off);
+            launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status, blocks_d, threads, st2,
+                        default_variant(SMCRT_FP64) + off);
+            cudaEventRecord(ev_join, st2);
+            cudaStreamWaitEvent(st, ev_join, 0);
+            cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
+            cudaStreamEndCapture(st, &g);
+            cudaGraphInstantiate(gen ? &b.graph_g : &b.graph, g, 0);
+            cudaGraphDestroy(g);
+        }
     }
 
     std::vector<std::shared_ptr<Job>> active;   // admitted, not yet complete
@@ -908,7 +951,9 @@ void scheduler(smcrt_ctx *ctx)
         const double dflt = nk ? known / nk : 2.0e5;
         const double share = round_cycles / (double)std::max(1, nfresh);
         int nm = 0, nd = 0;
+        bool general = false;
         for (auto &j : runnable) {
+            general = general || j->plan->host.general;
             const double c = j->cost > 0 ? j->cost : dflt;
             uint64_t q = (uint64_t)std::max(2048.0, share / c);
             if (!(j->cost > 0)) q = std::min<uint64_t>(q, 16384);   // unmeasured: a short first quantum
@@ -937,7 +982,7 @@ void scheduler(smcrt_ctx *ctx)
         for (int k = 0; k < nd; ++k) B.quanta += B.h_tab[kMaxSlots + k].end - B.h_tab[kMaxSlots + k].next;
         B.t_launch = now_s();
         cudaEventRecord(B.ev0, st);
-        cudaGraphLaunch(B.graph, st);
+        cudaGraphLaunch(general ? B.graph_g : B.graph, st);
         cudaEventRecord(B.ev, st);
         B.busy = true;
         B.idx = issued++;
@@ -959,6 +1004,7 @@ void scheduler(smcrt_ctx *ctx)
     cudaStreamSynchronize(st);
     for (auto &b : buf) {
         cudaGraphExecDestroy(b.graph);
+        cudaGraphExecDestroy(b.graph_g);
         cudaEventDestroy(b.ev);
         cudaEventDestroy(b.ev0);
         cudaFreeHost(b.h_tab);
@@ -1240,10 +1286,12 @@ int smcrt_submit(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *s
     j->prims.assign(scene->prims, scene->prims + scene->nprims);
     j->nodes.assign(scene->nodes, scene->nodes + scene->nnodes);
     j->regions.assign(scene->regions, scene->regions + scene->nregions);
+    if (scene->nxforms > 0) j->xforms.assign(scene->xforms, scene->xforms + scene->nxforms);
     j->scene = *scene;
     j->scene.prims = j->prims.data();
     j->scene.nodes = j->nodes.data();
     j->scene.regions = j->regions.data();
+    j->scene.xforms = scene->nxforms > 0 ? j->xforms.data() : nullptr;
     j->source = *source;
     j->grid = *grid;
     j->npackets = npackets;

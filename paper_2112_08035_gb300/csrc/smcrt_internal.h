@@ -22,6 +22,67 @@ constexpr int kAnalyticNormalMaxInstr = 4;
 constexpr int kCullMinPrims = 16;
 constexpr int kCullGrid = 16;   // packet kernels are compiled for <= 128 threads per block
 
+// Device primitive kind: the smcrt_prim_kind, plus this bit when the
+// primitive is evaluated in its own frame (smcrt_xform).  Instr.op carries
+// it in bits 8..15, the DevScene.pkind table as is.
+constexpr int32_t kXformFlag = 0x10;
+constexpr int kXf64 = 20;   // doubles per primitive frame: R (9), t (3), s, op, a (4), 2 unused
+constexpr int kXf32 = 5;    // float4 per primitive frame: R^T rows | t, (s, 1/s, op, 0), a
+
+inline int32_t device_kind(const smcrt_prim &P) { return P.kind | (P.xform > 0 ? kXformFlag : 0); }
+
+// The tables of primitive i: FP64 (8 doubles), FP32 (2 float4), and, when
+// xd / xf are given and the primitive has a frame, the frame (kXf64 doubles,
+// kXf32 float4).  Doubles are the caller's values or the reference's
+// expressions (capsule: b - a and |b - a|^2), so the FP64 kernel computes
+// with the same numbers as the oracle.
+inline void fill_prim(const smcrt_scene *sc, int i, double *d, float4 *f, double *xd, float4 *xf)
+{
+    const smcrt_prim &P = sc->prims[i];
+    for (int k = 0; k < 8; ++k) d[k] = 0.0;
+    f[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    f[1] = f[0];
+    if (P.kind == SMCRT_CAPSULE) {
+        const double bax = P.p[3] - P.p[0], bay = P.p[4] - P.p[1], baz = P.p[5] - P.p[2];
+        const double baba = bax * bax + bay * bay + baz * baz;
+        d[0] = P.p[0]; d[1] = P.p[1]; d[2] = P.p[2];
+        d[3] = bax; d[4] = bay; d[5] = baz; d[6] = P.p[6]; d[7] = baba;
+        f[0] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[6]);
+        f[1] = make_float4((float)bax, (float)bay, (float)baz, (float)(1.0 / baba));
+    } else if (P.kind == SMCRT_BOX) {
+        for (int k = 0; k < 6; ++k) d[k] = P.p[k];
+        f[0] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], 0.f);
+        f[1] = make_float4((float)P.p[3], (float)P.p[4], (float)P.p[5], 0.f);
+    } else if (P.kind == SMCRT_TORUS || P.kind == SMCRT_CYLINDER) {
+        for (int k = 0; k < 5; ++k) d[k] = P.p[k];
+        f[0] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[3]);
+        f[1] = make_float4((float)P.p[4], 0.f, 0.f, 0.f);
+    } else {
+        for (int k = 0; k < 4; ++k) d[k] = P.p[k];
+        f[0] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[3]);
+    }
+    if (xd == nullptr || xf == nullptr) return;
+    for (int k = 0; k < kXf64; ++k) xd[k] = 0.0;
+    for (int k = 0; k < kXf32; ++k) xf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P.xform <= 0) return;
+    const smcrt_xform &X = sc->xforms[P.xform - 1];
+    for (int k = 0; k < 9; ++k) xd[k] = X.rot[k];
+    for (int k = 0; k < 3; ++k) xd[9 + k] = X.t[k];
+    xd[12] = X.s;
+    xd[13] = (double)X.op;
+    for (int k = 0; k < 4; ++k) xd[14 + k] = X.a[k];
+    const double *R = X.rot;
+    xf[0] = make_float4((float)R[0], (float)R[3], (float)R[6], (float)X.t[0]);
+    xf[1] = make_float4((float)R[1], (float)R[4], (float)R[7], (float)X.t[1]);
+    xf[2] = make_float4((float)R[2], (float)R[5], (float)R[8], (float)X.t[2]);
+    xf[3] = make_float4((float)X.s, (float)(1.0 / X.s), (float)X.op, 0.f);
+    xf[4] = make_float4((float)X.a[0], (float)X.a[1], (float)X.a[2], (float)X.a[3]);
+}
+
+// Primitives the mixed kernel's analytic normal and the culling grid handle:
+// sphere, box, capsule in scene coordinates.
+inline bool plain_prim(const smcrt_prim &P) { return P.kind <= SMCRT_CAPSULE && P.xform <= 0; }
+
 // Segment stepping: the last instruction of a region whose program contains
 // a smooth union ("soft" region: its boundary is not made of primitive
 // boundaries, so only |d| bounds it) carries this bit in Instr.op.
@@ -107,6 +168,12 @@ struct DevScene {
     // Segment stepping (enum smcrt_stepping): the primitives of hard regions
     const int32_t *seg_prims;
     int32_t stepping, nseg;
+    // Primitive frames (kXf64 doubles / kXf32 float4 per primitive), null
+    // when no primitive has one
+    const double *xf64;
+    const float4 *xf32;
+    int32_t general;          // some primitive is a torus or cylinder or has a frame
+    int32_t general_pad;
     float h32;                // FP32 central-difference step for normals
     int64_t max_steps;
     // source

@@ -91,16 +91,17 @@ __device__ __forceinline__ double region_n64(const DevScene &S, int r)
 // and the Fresnel decision (uniform xi), reflected or refracted direction
 // and landing (land32), all in FP64.  A ray tangent in FP64 does not cross:
 // it stays on the near side with its direction unchanged.
+template <bool G>
 __device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, int rfar, float sg32, uint32_t xiw,
                                       float &px, float &py, float &pz, float &ux, float &uy, float &uz,
                                       float nx32, float ny32, float nz32)
 {
     const double x = px, y = py, z = pz;
     const double h = S.delta;
-    const double d0 = surface64(S, istar, x, y, z);
-    const double gx = surface64(S, istar, x + h, y, z) - d0;
-    const double gy = surface64(S, istar, x, y + h, z) - d0;
-    const double gz = surface64(S, istar, x, y, z + h) - d0;
+    const double d0 = surface64<G>(S, istar, x, y, z);
+    const double gx = surface64<G>(S, istar, x + h, y, z) - d0;
+    const double gy = surface64<G>(S, istar, x, y + h, z) - d0;
+    const double gz = surface64<G>(S, istar, x, y, z + h) - d0;
     double nx = nx32, ny = ny32, nz = nz32;
     const double l2 = gx * gx + gy * gy + gz * gz;
     if (l2 > 0.0) {
@@ -169,6 +170,7 @@ struct WarpShared {
 //   4 the track-length tally of this iteration's move (one call site),
 //   5 one Philox call serving launch, interaction and Fresnel draws,
 //   6 the consumers: release a packet, scatter (HG + roulette), Fresnel.
+template <bool G>
 __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
                              int lane)
 {
@@ -271,7 +273,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             const float e = (phase == kFar ? 2.f : -2.f) * delta * sg;
             ex = qx + e * nx; ey = qy + e * ny; ez = qz + e * nz;
         }
-        const Eval32 E = scene_eval32(S, ex, ey, ez, sel);
+        const Eval32 E = scene_eval32<G>(S, ex, ey, ez, sel);
         {
             const unsigned ev = __ballot_sync(SMCRT_FULL, alive && phase != kLaunch);
             if (lane == 0) wadd(wa, kEvals, __popc(ev));
@@ -375,7 +377,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             }
             interact = mu_t > 0.f && tau < mu_t * L;
             if (seg_step && !interact) {           // segment stepping: a longer move along u
-                L = fmaxf(L, segment_bound32(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
+                L = fmaxf(L, segment_bound32<G>(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
                 interact = mu_t > 0.f && tau < mu_t * L;
             }
             const float seg = interact ? tau * imu_t : L;
@@ -465,7 +467,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             const bool curved_noisy = !S.analytic_nrm && zeros != 2;   // probe normals on curved faces
             if (ci < kGrazeCos || fabsf(st2 - 1.f) < kCritBand || curved_noisy) {
                 wadd(wa, kRefined, 1);
-                refine64(S, istar, rnear, rfar, sg, r.x, qx, qy, qz, ux, uy, uz, nx, ny, nz);
+                refine64<G>(S, istar, rnear, rfar, sg, r.x, qx, qy, qz, ux, uy, uz, nx, ny, nz);
                 px = qx; py = qy; pz = qz;
             } else {                               // planar face: the FP32 normal is exact
                 float R = 1.f, ct = 0.f;
@@ -543,7 +545,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
     if (lane == 0) wadd(wa, kPieces, pc);
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, bool G>
 __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, int njobs, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -577,10 +579,14 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
         const long long *s8 = reinterpret_cast<const long long *>(src);
         long long *d8 = reinterpret_cast<long long *>(&ws->S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+        if (!G && ws->S.general) {           // a scene with general shapes needs the G instantiation
+            if (lane == 0) atomicOr(status, kStatusBadJob);
+            continue;
+        }
         if (lane == 0) jobconst_fill(&ws->jc, J);
         wacc_clear(&ws->acc, lane);
         const long long t0 = clock64();
-        run_job_mixed(ws->S, &ws->acc, &ws->jc, J, lane);
+        run_job_mixed<G>(ws->S, &ws->acc, &ws->jc, J, lane);
         __syncwarp();
         if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
         wacc_flush(&ws->acc, J->totals, lane);
@@ -591,7 +597,9 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
 
 // Register budgets of the instantiations: variant v keeps kMinBlocks
 // blocks of 128 threads resident per SM (more blocks = fewer registers per
-// thread, possibly spilled); the autotuner picks per scene.
+// thread, possibly spilled); the autotuner picks per scene.  Variants
+// kNumVariants .. 2 kNumVariants - 1 are the same budgets for scenes with
+// general shapes (tori, cylinders, primitive frames).
 constexpr int kVariantBlocks[kNumVariants] = {5, 4, 3};
 
 cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream,
@@ -599,9 +607,12 @@ cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int 
 {
     const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
     switch (variant) {
-    case 1: packets_mixed<4><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
-    case 2: packets_mixed<3><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
-    default: packets_mixed<5><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 1: packets_mixed<4, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 2: packets_mixed<3, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 3: packets_mixed<5, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 4: packets_mixed<4, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 5: packets_mixed<3, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    default: packets_mixed<5, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
     }
     return cudaGetLastError();
 }
@@ -611,9 +622,12 @@ int occupancy_mixed(int threads, int variant)
     int n = 0;
     const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
     switch (variant) {
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<4>, threads, sm); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<3>, threads, sm); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<5>, threads, sm); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<4, false>, threads, sm); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<3, false>, threads, sm); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<5, true>, threads, sm); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<4, true>, threads, sm); break;
+    case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<3, true>, threads, sm); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed<5, false>, threads, sm); break;
     }
     return n;
 }

@@ -61,6 +61,7 @@ struct WarpShared {
 // every floating-point operation the reference algorithm's, in its order:
 // the oracle's run of a packet is a sequence of the same IEEE operations on
 // the same values, so its tallies come out bit for bit.
+template <bool G>
 __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
                              int lane)
 {
@@ -154,7 +155,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
         } else if (phase == kNear) {
             ex = qx - ee * nx; ey = qy - ee * ny; ez = qz - ee * nz;
         }
-        const Eval64 E = scene_eval64(S, ex, ey, ez, sel);
+        const Eval64 E = scene_eval64<G>(S, ex, ey, ez, sel);
         {
             const unsigned ev = __ballot_sync(SMCRT_FULL, alive && phase != kLaunch);
             if (lane == 0) wadd(wa, kEvals, __popc(ev));
@@ -264,7 +265,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
             if (reg >= 0) mu_t = __ldg(S.reg64 + 8 * reg + 4);
             interact = mu_t > 0.0 && tau < mu_t * L;
             if (seg_step && !interact) {           // segment stepping: a longer move along u
-                L = fmax(L, segment_bound64(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
+                L = fmax(L, segment_bound64<G>(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
                 interact = mu_t > 0.0 && tau < mu_t * L;
             }
             const double seg = interact ? tau / mu_t : L;
@@ -401,7 +402,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
     if (lane == 0) wadd(wa, kPieces, pc);
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, bool G>
 __global__ void __launch_bounds__(128, kMinBlocks) packets_fp64(JobWork *jobs, int njobs, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -435,10 +436,14 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_fp64(JobWork *jobs, i
         const long long *s8 = reinterpret_cast<const long long *>(src);
         long long *d8 = reinterpret_cast<long long *>(&ws->S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+        if (!G && ws->S.general) {           // a scene with general shapes needs the G instantiation
+            if (lane == 0) atomicOr(status, kStatusBadJob);
+            continue;
+        }
         if (lane == 0) jobconst_fill(&ws->jc, J);
         wacc_clear(&ws->acc, lane);
         const long long t0 = clock64();
-        run_job_fp64(ws->S, &ws->acc, &ws->jc, J, lane);
+        run_job_fp64<G>(ws->S, &ws->acc, &ws->jc, J, lane);
         __syncwarp();
         if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
         wacc_flush(&ws->acc, J->totals, lane);
@@ -456,10 +461,13 @@ cudaError_t launch_fp64(JobWork *jobs, int njobs, int *status, int blocks, int t
                         int variant)
 {
     const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
-    switch (variant) {
-    case 1: packets_fp64<3><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
-    case 2: packets_fp64<2><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
-    default: packets_fp64<4><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    switch (variant) {   // kNumVariants and up: the same budgets for scenes with general shapes
+    case 1: packets_fp64<3, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 2: packets_fp64<2, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 3: packets_fp64<4, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 4: packets_fp64<3, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 5: packets_fp64<2, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    default: packets_fp64<4, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
     }
     return cudaGetLastError();
 }
@@ -469,9 +477,12 @@ int occupancy_fp64(int threads, int variant)
     int n = 0;
     const size_t sm = (size_t)(threads / 32) * sizeof(WarpShared);
     switch (variant) {
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<3>, threads, sm); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<2>, threads, sm); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<4>, threads, sm); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<3, false>, threads, sm); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<2, false>, threads, sm); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<4, true>, threads, sm); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<3, true>, threads, sm); break;
+    case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<2, true>, threads, sm); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_fp64<4, false>, threads, sm); break;
     }
     return n;
 }

@@ -175,37 +175,158 @@ __device__ __forceinline__ float box32(float x, float y, float z, float cx, floa
     return outside + inside;
 }
 
-__device__ __forceinline__ double prim64(const DevScene &S, int kind, int i, double x, double y, double z)
+// Torus (kind 3) and capped cylinder (kind 4), out of line: they are rare,
+// and inlined copies would cost the hot loop registers.
+static __device__ __noinline__ double round64(int kind, const double *P, double x, double y, double z)
 {
-    const double *P = S.p64 + 8 * i;
+    const double dx = x - __ldg(P), dy = y - __ldg(P + 1), dz = z - __ldg(P + 2);
+    if (kind == 3) {                     // torus about z: core circle distance - tube radius
+        const double ring = sqrt(dx * dx + dy * dy) - __ldg(P + 3);
+        return sqrt(ring * ring + dz * dz) - __ldg(P + 4);
+    }
+    const double a = sqrt(dx * dx + dy * dy) - __ldg(P + 3);   // capped cylinder along z
+    const double b = fabs(dz) - __ldg(P + 4);
+    const double ma = fmax(a, 0.0), mb = fmax(b, 0.0);
+    return fmin(fmax(a, b), 0.0) + sqrt(ma * ma + mb * mb);
+}
+
+// Primitive distances in local coordinates (kind 0..4, Sec. 2.2 and the
+// Fig. 1 basic shapes).  FP64: the reference's operations in its order.
+// G = false: the scene has only spheres, boxes and capsules in scene
+// coordinates (the kernels are instantiated for both cases, so plain
+// scenes pay nothing for the general shapes).
+template <bool G>
+__device__ __forceinline__ double base64(int kind, const double *P, double x, double y, double z)
+{
     if (kind == 0) {
         const double dx = x - __ldg(P), dy = y - __ldg(P + 1), dz = z - __ldg(P + 2);
         return sqrt(dx * dx + dy * dy + dz * dz) - __ldg(P + 3);
     }
     if (kind == 1)
         return box64(x, y, z, __ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5));
-    const double pax = x - __ldg(P), pay = y - __ldg(P + 1), paz = z - __ldg(P + 2);
-    const double bax = __ldg(P + 3), bay = __ldg(P + 4), baz = __ldg(P + 5);
-    double t = (pax * bax + pay * bay + paz * baz) / __ldg(P + 7);
-    t = fmin(fmax(t, 0.0), 1.0);
-    const double dx = pax - bax * t, dy = pay - bay * t, dz = paz - baz * t;
-    return sqrt(dx * dx + dy * dy + dz * dz) - __ldg(P + 6);
+    if (!G || kind == 2) {
+        const double pax = x - __ldg(P), pay = y - __ldg(P + 1), paz = z - __ldg(P + 2);
+        const double bax = __ldg(P + 3), bay = __ldg(P + 4), baz = __ldg(P + 5);
+        double t = (pax * bax + pay * bay + paz * baz) / __ldg(P + 7);
+        t = fmin(fmax(t, 0.0), 1.0);
+        const double dx = pax - bax * t, dy = pay - bay * t, dz = paz - baz * t;
+        return sqrt(dx * dx + dy * dy + dz * dz) - __ldg(P + 6);
+    }
+    return round64(kind, P, x, y, z);
 }
 
-__device__ __forceinline__ float prim32(const DevScene &S, int kind, int i, float x, float y, float z)
+// A primitive in its frame (smcrt_xform): local point R^T (p - t) / s, the
+// domain operation, the local distance scaled back by s and divided by the
+// operation's Lipschitz bound.
+static __device__ __noinline__ double xprim64(const DevScene &S, int kind, int i, double x, double y, double z)
 {
-    const float4 A = __ldg(S.p32 + 2 * i);
+    const double *X = S.xf64 + kXf64 * i;
+    const double vx = x - __ldg(X + 9), vy = y - __ldg(X + 10), vz = z - __ldg(X + 11);
+    const double s = __ldg(X + 12);
+    double q0 = (__ldg(X) * vx + __ldg(X + 3) * vy + __ldg(X + 6) * vz) / s;
+    double q1 = (__ldg(X + 1) * vx + __ldg(X + 4) * vy + __ldg(X + 7) * vz) / s;
+    double q2 = (__ldg(X + 2) * vx + __ldg(X + 5) * vy + __ldg(X + 8) * vz) / s;
+    const int op = (int)__ldg(X + 13);
+    const double a0 = __ldg(X + 14), a1 = __ldg(X + 15), a2 = __ldg(X + 16), a3 = __ldg(X + 17);
+    double L = 1.0;
+    if (op == 1) {                       // elongate
+        q0 = q0 - fmin(fmax(q0, -a0), a0);
+        q1 = q1 - fmin(fmax(q1, -a1), a1);
+        q2 = q2 - fmin(fmax(q2, -a2), a2);
+    } else if (op == 2 || op == 3) {     // twist about z / bend in x-y
+        const double rho = sqrt(q0 * q0 + q1 * q1);
+        double sn, cs;
+        sincos2pi64(a0 * (op == 2 ? q2 : q0), &sn, &cs);
+        const double rx = cs * q0 - sn * q1;
+        const double ry = sn * q0 + cs * q1;
+        q0 = rx; q1 = ry;
+        const double m = 6.283185307179586 * a0 * fmax(rho, a1);   // stretch bound of the map
+        L = op == 2 ? 0.5 * (m + sqrt(m * m + 4.0)) : 1.0 + m;
+    } else if (op == 4) {                // repetition: nearest copy
+        if (a0 > 0.0) { double k = floor(q0 / a0 + 0.5); k = fmin(fmax(k, -a3), a3); q0 = q0 - a0 * k; }
+        if (a1 > 0.0) { double k = floor(q1 / a1 + 0.5); k = fmin(fmax(k, -a3), a3); q1 = q1 - a1 * k; }
+        if (a2 > 0.0) { double k = floor(q2 / a2 + 0.5); k = fmin(fmax(k, -a3), a3); q2 = q2 - a2 * k; }
+    }
+    return s * base64<true>(kind, S.p64 + 8 * i, q0, q1, q2) / L;
+}
+
+template <bool G>
+__device__ __forceinline__ double prim64(const DevScene &S, int kind, int i, double x, double y, double z)
+{
+    if (G && (kind & kXformFlag)) return xprim64(S, kind & 0xf, i, x, y, z);
+    return base64<G>(kind, S.p64 + 8 * i, x, y, z);
+}
+
+static __device__ __noinline__ float round32(int kind, const float4 *P, float x, float y, float z)
+{
+    const float4 A = __ldg(P), B = __ldg(P + 1);
+    const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
+    if (kind == 3) {
+        const float ring = sqrtf(dx * dx + dy * dy) - A.w;
+        return sqrtf(ring * ring + dz * dz) - B.x;
+    }
+    const float a = sqrtf(dx * dx + dy * dy) - A.w;
+    const float b = fabsf(dz) - B.x;
+    const float ma = fmaxf(a, 0.f), mb = fmaxf(b, 0.f);
+    return fminf(fmaxf(a, b), 0.f) + sqrtf(ma * ma + mb * mb);
+}
+
+template <bool G>
+__device__ __forceinline__ float base32(int kind, const float4 *P, float x, float y, float z)
+{
+    const float4 A = __ldg(P);
     if (kind == 0) {
         const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
         return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
     }
-    const float4 B = __ldg(S.p32 + 2 * i + 1);
+    const float4 B = __ldg(P + 1);
     if (kind == 1) return box32(x, y, z, A.x, A.y, A.z, B.x, B.y, B.z);
-    const float pax = x - A.x, pay = y - A.y, paz = z - A.z;
-    float t = (pax * B.x + pay * B.y + paz * B.z) * B.w;
-    t = fminf(fmaxf(t, 0.f), 1.f);
-    const float dx = pax - B.x * t, dy = pay - B.y * t, dz = paz - B.z * t;
-    return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
+    if (!G || kind == 2) {
+        const float pax = x - A.x, pay = y - A.y, paz = z - A.z;
+        float t = (pax * B.x + pay * B.y + paz * B.z) * B.w;
+        t = fminf(fmaxf(t, 0.f), 1.f);
+        const float dx = pax - B.x * t, dy = pay - B.y * t, dz = paz - B.z * t;
+        return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
+    }
+    return round32(kind, P, x, y, z);
+}
+
+static __device__ __noinline__ float xprim32(const DevScene &S, int kind, int i, float x, float y, float z)
+{
+    const float4 *X = S.xf32 + kXf32 * i;
+    const float4 R0 = __ldg(X), R1 = __ldg(X + 1), R2 = __ldg(X + 2), SC = __ldg(X + 3), A = __ldg(X + 4);
+    const float vx = x - R0.w, vy = y - R1.w, vz = z - R2.w;
+    float q0 = (R0.x * vx + R0.y * vy + R0.z * vz) * SC.y;
+    float q1 = (R1.x * vx + R1.y * vy + R1.z * vz) * SC.y;
+    float q2 = (R2.x * vx + R2.y * vy + R2.z * vz) * SC.y;
+    const int op = (int)SC.z;
+    float L = 1.f;
+    if (op == 1) {
+        q0 = q0 - fminf(fmaxf(q0, -A.x), A.x);
+        q1 = q1 - fminf(fmaxf(q1, -A.y), A.y);
+        q2 = q2 - fminf(fmaxf(q2, -A.z), A.z);
+    } else if (op == 2 || op == 3) {
+        const float rho = sqrtf(q0 * q0 + q1 * q1);
+        float sn, cs;
+        sincospif(2.f * A.x * (op == 2 ? q2 : q0), &sn, &cs);
+        const float rx = cs * q0 - sn * q1;
+        const float ry = sn * q0 + cs * q1;
+        q0 = rx; q1 = ry;
+        const float m = 6.2831853f * A.x * fmaxf(rho, A.y);
+        L = op == 2 ? 0.5f * (m + sqrtf(m * m + 4.f)) : 1.f + m;
+    } else if (op == 4) {
+        if (A.x > 0.f) { float k = floorf(q0 / A.x + 0.5f); k = fminf(fmaxf(k, -A.w), A.w); q0 = q0 - A.x * k; }
+        if (A.y > 0.f) { float k = floorf(q1 / A.y + 0.5f); k = fminf(fmaxf(k, -A.w), A.w); q1 = q1 - A.y * k; }
+        if (A.z > 0.f) { float k = floorf(q2 / A.z + 0.5f); k = fminf(fmaxf(k, -A.w), A.w); q2 = q2 - A.z * k; }
+    }
+    return SC.x * base32<true>(kind, S.p32 + 2 * i, q0, q1, q2) / L;
+}
+
+template <bool G>
+__device__ __forceinline__ float prim32(const DevScene &S, int kind, int i, float x, float y, float z)
+{
+    if (G && (kind & kXformFlag)) return xprim32(S, kind & 0xf, i, x, y, z);
+    return base32<G>(kind, S.p32 + 2 * i, x, y, z);
 }
 
 // a = left (earlier) operand, b = right.  Smooth union: polynomial smooth
@@ -235,7 +356,7 @@ __device__ __forceinline__ float csg32(int op, float a, float b, float kinv)
 
 // Evaluate instructions [i0, i1) as a register-stack program; when `full`,
 // record every region end (region, d_min, istar, and d of surface `sel`).
-template <bool kFull>
+template <bool kFull, bool G>
 __device__ __forceinline__ double run_prog64(const DevScene &S, int i0, int i1, double x, double y, double z,
                                              int sel, Eval64 *E)
 {
@@ -244,7 +365,7 @@ __device__ __forceinline__ double run_prog64(const DevScene &S, int i0, int i1, 
         const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
         const int op = ins.x & 0xff, kind = (ins.x >> 8) & 0xff;
         double v = 0.0;
-        if (ins.y >= 0) v = prim64(S, kind, ins.y, x, y, z);
+        if (ins.y >= 0) v = prim64<G>(S, kind, ins.y, x, y, z);
         if (op == 0) {
             s3 = s2; s2 = s1; s1 = s0; s0 = v;
         } else {
@@ -268,7 +389,7 @@ __device__ __forceinline__ double run_prog64(const DevScene &S, int i0, int i1, 
     return s0;
 }
 
-template <bool kFull>
+template <bool kFull, bool G>
 __device__ __forceinline__ float run_prog32(const DevScene &S, int i0, int i1, float x, float y, float z,
                                             int sel, Eval32 *E)
 {
@@ -277,7 +398,7 @@ __device__ __forceinline__ float run_prog32(const DevScene &S, int i0, int i1, f
         const int4 ins = __ldg(reinterpret_cast<const int4 *>(S.instr) + i);
         const int op = ins.x & 0xff, kind = (ins.x >> 8) & 0xff;
         float v = 0.f;
-        if (ins.y >= 0) v = prim32(S, kind, ins.y, x, y, z);
+        if (ins.y >= 0) v = prim32<G>(S, kind, ins.y, x, y, z);
         if (op == 0) {
             s3 = s2; s2 = s1; s1 = s0; s0 = v;
         } else {
@@ -302,13 +423,14 @@ __device__ __forceinline__ float run_prog32(const DevScene &S, int i0, int i1, f
 }
 
 // Full scene evaluation (Sec. 2.3): every region, then the bounding box.
+template <bool G>
 __device__ __forceinline__ Eval64 scene_eval64(const DevScene &S, double x, double y, double z, int sel)
 {
     Eval64 E;
     E.dmin = __longlong_as_double(0x7ff0000000000000LL);
     E.dsoft = E.dmin;
     E.dstar = 0.0; E.dsel = 0.0; E.istar = -1; E.region = -1;
-    run_prog64<true>(S, 0, S.ninstr, x, y, z, sel, &E);
+    run_prog64<true, G>(S, 0, S.ninstr, x, y, z, sel, &E);
     const double db = box64(x, y, z, S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2]);
     E.dbox = db;
     if (fabs(db) < E.dmin) { E.dmin = fabs(db); E.istar = -1; E.dstar = db; }
@@ -331,10 +453,10 @@ __device__ __forceinline__ float culled_region32(const DevScene &S, float x, flo
     const int o0 = __ldg(S.cull_off + c), o1 = __ldg(S.cull_off + c + 1);
     if (o1 <= o0) return S.cull_rmax;
     int i = __ldg(S.cull_list + o0);
-    float acc = prim32(S, __ldg(S.pkind + i), i, x, y, z);
+    float acc = prim32<false>(S, __ldg(S.pkind + i), i, x, y, z);   // culled regions are plain
     for (int j = o0 + 1; j < o1; ++j) {
         i = __ldg(S.cull_list + j);
-        acc = csg32(S.cull_op, acc, prim32(S, __ldg(S.pkind + i), i, x, y, z), S.cull_kinv);
+        acc = csg32(S.cull_op, acc, prim32<false>(S, __ldg(S.pkind + i), i, x, y, z), S.cull_kinv);
     }
     return fminf(acc, S.cull_rmax);
 }
@@ -348,6 +470,7 @@ __device__ __forceinline__ void region_end32(Eval32 *E, int r, float d, int sel,
     if (r == sel) E->dsel = d;
 }
 
+template <bool G>
 __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float y, float z, int sel)
 {
     Eval32 E;
@@ -355,12 +478,12 @@ __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float
     E.dsoft = E.dmin;
     E.dstar = 0.f; E.dsel = 0.f; E.istar = -1; E.region = -1;
     if (S.cull_region < 0) {
-        run_prog32<true>(S, 0, S.ninstr, x, y, z, sel, &E);
+        run_prog32<true, G>(S, 0, S.ninstr, x, y, z, sel, &E);
     } else {   // regions in index order: before, the culled one, after
         const int2 rr = __ldg(S.rrange + S.cull_region);
-        run_prog32<true>(S, 0, rr.x, x, y, z, sel, &E);
+        run_prog32<true, G>(S, 0, rr.x, x, y, z, sel, &E);
         region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, S.cull_op == 2);
-        run_prog32<true>(S, rr.y, S.ninstr, x, y, z, sel, &E);
+        run_prog32<true, G>(S, rr.y, S.ninstr, x, y, z, sel, &E);
     }
     const float db = box32(x, y, z, S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2]);
     E.dbox = db;
@@ -470,11 +593,12 @@ static __device__ __noinline__ float grad_surface32(const DevScene &S, int r, fl
 }
 
 // SDF of one surface in FP64 (region program, or the bounding box for -1).
+template <bool G>
 __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, double y, double z)
 {
     if (r < 0) return box64(x, y, z, S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2]);
     const int2 rr = __ldg(S.rrange + r);
-    return run_prog64<false>(S, rr.x, rr.y, x, y, z, -2, nullptr);
+    return run_prog64<false, G>(S, rr.x, rr.y, x, y, z, -2, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -533,6 +657,7 @@ __device__ __forceinline__ double seg_box64(double cx, double cy, double cz, dou
     return tf > 0.0 ? tf : 0.0;          // inside: exit of the shrunk box
 }
 
+template <bool G>
 static __device__ __noinline__ double segment_bound64(const DevScene &S, double dsoft, double dbox, double px,
                                                       double py, double pz, double ux, double uy, double uz)
 {
@@ -541,7 +666,7 @@ static __device__ __noinline__ double segment_bound64(const DevScene &S, double 
     for (int j = 0; j < S.nseg; ++j) {
         const int i = __ldg(S.seg_prims + j);
         const int kind = __ldg(S.pkind + i);
-        const double d = prim64(S, kind, i, px, py, pz);
+        const double d = prim64<G>(S, kind, i, px, py, pz);
         double b;
         if (!(fabs(d) > dh)) {
             b = 0.0;
@@ -607,6 +732,7 @@ __device__ __forceinline__ float seg_box32(float cx, float cy, float cz, float h
     return tf > 0.f ? tf : 0.f;
 }
 
+template <bool G>
 static __device__ __noinline__ float segment_bound32(const DevScene &S, float dsoft, float dbox, float px,
                                                      float py, float pz, float ux, float uy, float uz)
 {
@@ -616,7 +742,7 @@ static __device__ __noinline__ float segment_bound32(const DevScene &S, float ds
     for (int j = 0; j < S.nseg; ++j) {
         const int i = __ldg(S.seg_prims + j);
         const int kind = __ldg(S.pkind + i);
-        const float d = prim32(S, kind, i, px, py, pz);
+        const float d = prim32<G>(S, kind, i, px, py, pz);
         float b;
         if (!(fabsf(d) > dh)) {
             b = 0.f;

@@ -80,7 +80,7 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
             if (op == SMCRT_OP_PRIM) {
                 const int p = nd[i].prim;
                 if (p < 0 || p >= sc->nprims) return SMCRT_ERR_BAD_SCENE;
-                const int kind = sc->prims[p].kind;
+                const int kind = device_kind(sc->prims[p]);
                 const bool fuse = depth >= 1 && i + 1 < R.node_count && nd[i + 1].op >= SMCRT_OP_UNION &&
                                   nd[i + 1].op <= SMCRT_OP_SUBTRACT;
                 in.prim = p;
@@ -137,32 +137,21 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     int32_t segp[kMaxPrims];
     const int nseg = sc->stepping == SMCRT_STEP_SEGMENT ? hard_region_prims(sc, segp) : 0;
     const size_t o_seg = take(sizeof(int32_t) * nseg);
+    const bool has_xf = sc->nxforms > 0;
+    const size_t o_xf64 = take(has_xf ? sizeof(double) * kXf64 * np : 0);
+    const size_t o_xf32 = take(has_xf ? sizeof(float4) * kXf32 * np : 0);
     if (kImageOff + off > kNoAllocScratchBytes) return SMCRT_ERR_NO_MEMORY;
     std::memset(img, 0, off);
 
     int32_t *pkind = (int32_t *)(img + o_kind);
     double *p64 = (double *)(img + o_p64);
     float4 *p32 = (float4 *)(img + o_p32);
+    double *xf64 = has_xf ? (double *)(img + o_xf64) : nullptr;
+    float4 *xf32 = has_xf ? (float4 *)(img + o_xf32) : nullptr;
     for (int i = 0; i < np; ++i) {
-        const smcrt_prim &P = sc->prims[i];
-        pkind[i] = P.kind;
-        double *d = p64 + 8 * i;
-        if (P.kind == SMCRT_CAPSULE) {
-            const double bax = P.p[3] - P.p[0], bay = P.p[4] - P.p[1], baz = P.p[5] - P.p[2];
-            const double baba = bax * bax + bay * bay + baz * baz;
-            d[0] = P.p[0]; d[1] = P.p[1]; d[2] = P.p[2];
-            d[3] = bax; d[4] = bay; d[5] = baz; d[6] = P.p[6]; d[7] = baba;
-            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[6]);
-            p32[2 * i + 1] = make_float4((float)bax, (float)bay, (float)baz, (float)(1.0 / baba));
-        } else if (P.kind == SMCRT_BOX) {
-            for (int k = 0; k < 6; ++k) d[k] = P.p[k];
-            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], 0.f);
-            p32[2 * i + 1] = make_float4((float)P.p[3], (float)P.p[4], (float)P.p[5], 0.f);
-        } else {
-            for (int k = 0; k < 4; ++k) d[k] = P.p[k];
-            p32[2 * i] = make_float4((float)P.p[0], (float)P.p[1], (float)P.p[2], (float)P.p[3]);
-            p32[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        pkind[i] = device_kind(sc->prims[i]);
+        fill_prim(sc, i, p64 + 8 * i, p32 + 2 * i, has_xf ? xf64 + kXf64 * i : nullptr,
+                  has_xf ? xf32 + kXf32 * i : nullptr);
     }
     double *reg64 = (double *)(img + o_r64);
     float4 *reg32 = (float4 *)(img + o_r32);
@@ -210,9 +199,15 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     H.stepping = sc->stepping;
     H.nseg = nseg;
     H.seg_prims = nseg > 0 ? (const int32_t *)(base + o_seg) : nullptr;
+    H.xf64 = has_xf ? (const double *)(base + o_xf64) : nullptr;
+    H.xf32 = has_xf ? (const float4 *)(base + o_xf32) : nullptr;
+    for (int i = 0; i < np; ++i) H.general = H.general || !plain_prim(sc->prims[i]);
     {
         int longest = 0;
+        bool plain = true;
+        for (int i = 0; i < np; ++i) plain = plain && plain_prim(sc->prims[i]);
         for (int r = 0; r < nr; ++r) longest = (rr[r].y - rr[r].x) > longest ? (rr[r].y - rr[r].x) : longest;
+        if (!plain) longest = kAnalyticNormalMaxInstr + 1;   // probe normals for other shapes and frames
         H.analytic_nrm = longest <= kAnalyticNormalMaxInstr ? 1 : 0;
     }
     H.delta32 = std::fmax((float)sc->delta, 64.f * ulp32(rmax));
@@ -309,7 +304,9 @@ extern "C" int smcrt_run_noalloc(const smcrt_scene *scene, const smcrt_source *s
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SMCRT_ERR_CUDA;
     const int threads = 128;
-    const int variant = precision == SMCRT_FP64 ? 1 : 0;
+    bool general = false;   // tori, cylinders, frames: the general-shape instantiation
+    for (int i = 0; i < scene->nprims; ++i) general = general || !plain_prim(scene->prims[i]);
+    const int variant = (precision == SMCRT_FP64 ? 1 : 0) + (general ? kNumVariants : 0);
     const int occ = precision == SMCRT_FP64 ? occupancy_fp64(threads, variant) : occupancy_mixed(threads, variant);
     const int blocks = sms * (occ > 0 ? occ : 1);
     const cudaError_t e = precision == SMCRT_FP64

@@ -38,16 +38,16 @@ def test_library_exports_every_declared_function():
 def test_struct_layouts_match_header(tmp_path):
     probe = tmp_path / "probe.c"
     probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "smcrt.h"\n'
-                     "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+                     "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
                      "sizeof(smcrt_prim), sizeof(smcrt_csg_node), sizeof(smcrt_region), sizeof(smcrt_scene),"
                      "sizeof(smcrt_source), sizeof(smcrt_grid), sizeof(smcrt_totals), sizeof(smcrt_packet_record),"
-                     "offsetof(smcrt_scene, delta));return 0;}\n")
+                     "offsetof(smcrt_scene, delta), sizeof(smcrt_xform), offsetof(smcrt_scene, xforms));return 0;}\n")
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(smc.Prim), C.sizeof(smc.CsgNode), C.sizeof(smc.Region), C.sizeof(smc.Scene),
             C.sizeof(smc.Source), C.sizeof(smc.Grid), C.sizeof(smc.Totals), smc.RECORD_DTYPE.itemsize,
-            smc.Scene.delta.offset]
+            smc.Scene.delta.offset, C.sizeof(smc.Xform), smc.Scene.xforms.offset]
     assert got == want
 
 

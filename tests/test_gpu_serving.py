@@ -28,7 +28,8 @@ def _jobs():
             W.glass_container(50_000, 13, "mixed", grid_n=50), W.vessel_network(5_000, 3, "mixed", grid_n=50),
             W.sphere_pencil(20_000, 14, "fp64"), W.three_layer_slab(7, 15, "fp64", grid_n=10),
             W.glass_container(40_000, 16, "mixed", grid_n=50).with_stepping(W.SEGMENT),
-            W.three_layer_slab(3_000, 17, "fp64", grid_n=20).with_stepping(W.SEGMENT)]
+            W.three_layer_slab(3_000, 17, "fp64", grid_n=20).with_stepping(W.SEGMENT),
+            W.sdf_gallery(20_000, 18, "mixed", grid_n=20), W.sdf_gallery(300, 19, "fp64", grid_n=12)]
 
 
 def test_same_result_alone_and_in_the_mix(ctx):

@@ -168,6 +168,182 @@ def test_csg_semantics():
                             [W.Node(W.PRIM, 0), W.Node(W.PRIM, 1), W.Node(W.SMOOTH_UNION, -1, k)])
     assert abs(O.region_sdf(sc2, 0, mid) - (e1 - k / 4)) < 1e-14
 
+# --------------------------------------------------------------------------
+# More primitives, frames and domain operations (Sec. 2.2, Fig. 1 gallery).
+# --------------------------------------------------------------------------
+
+def _sdf(prim, p):
+    return O.region_sdf(_one_region_scene([prim], W.prim_program([0])), 0, p)
+
+
+def test_torus_sdf_brute_force():
+    c, R, r = np.array([0.2, -0.1, 0.3]), 0.6, 0.2
+    prim = W.Prim(W.TORUS, tuple(c) + (R, r))
+    # dense parametric sample of the surface
+    u, v = np.meshgrid(np.linspace(0, 2 * np.pi, 721), np.linspace(0, 2 * np.pi, 241))
+    surf = np.stack([(R + r * np.cos(v)) * np.cos(u), (R + r * np.cos(v)) * np.sin(u), r * np.sin(v)], -1)
+    surf = surf.reshape(-1, 3) + c
+    spacing = 2 * np.pi * (R + r) / 720
+    rng = np.random.default_rng(11)
+    for p in rng.uniform(-1.2, 1.2, (120, 3)) + c:
+        q = p - c
+        inside = (math.hypot(q[0], q[1]) - R) ** 2 + q[2] ** 2 < r * r
+        d = _sdf(prim, p)
+        assert (d < 0) == inside
+        assert abs(abs(d) - np.sqrt(((surf - p) ** 2).sum(1)).min()) <= spacing, p
+
+
+def test_cylinder_sdf_brute_force():
+    c, r, h = np.array([-0.1, 0.2, 0.0]), 0.4, 0.3
+    prim = W.Prim(W.CYLINDER, tuple(c) + (r, h))
+    u, z = np.meshgrid(np.linspace(0, 2 * np.pi, 481), np.linspace(-h, h, 121))
+    side = np.stack([r * np.cos(u), r * np.sin(u), z], -1).reshape(-1, 3)
+    uu, rr = np.meshgrid(np.linspace(0, 2 * np.pi, 481), np.linspace(0, r, 81))
+    caps = [np.stack([rr * np.cos(uu), rr * np.sin(uu), np.full_like(rr, s * h)], -1).reshape(-1, 3)
+            for s in (-1, 1)]
+    surf = np.concatenate([side] + caps) + c
+    spacing = 2 * np.pi * r / 480 + 2 * h / 120
+    rng = np.random.default_rng(12)
+    for p in rng.uniform(-1.0, 1.0, (120, 3)) + c:
+        q = p - c
+        inside = math.hypot(q[0], q[1]) < r and abs(q[2]) < h
+        d = _sdf(prim, p)
+        assert (d < 0) == inside
+        assert abs(abs(d) - np.sqrt(((surf - p) ** 2).sum(1)).min()) <= spacing, p
+
+
+def test_rigid_frame_box_brute_force():
+    # a box placed by a rotation about an oblique axis, a translation and a
+    # uniform scale: its distance is the distance to the placed surface
+    h = np.array([0.5, 0.2, 0.3])
+    X = W.Xform(rot=W.rotation((1.0, 2.0, -0.5), 37.0), t=(0.3, -0.4, 0.2), s=1.3)
+    prim = W.Prim(W.BOX, (0.0, 0.0, 0.0) + tuple(h), X)
+    Rm = np.array(X.rot).reshape(3, 3)
+    m = 121
+    a = np.linspace(-1, 1, m)
+    A, B = np.meshgrid(a, a)
+    faces = []
+    for ax in range(3):
+        o = [k for k in range(3) if k != ax]
+        for sgn in (-1, 1):
+            f = np.zeros((m * m, 3))
+            f[:, ax] = sgn * h[ax]
+            f[:, o[0]] = A.ravel() * h[o[0]]
+            f[:, o[1]] = B.ravel() * h[o[1]]
+            faces.append(f)
+    surf = X.s * np.concatenate(faces) @ Rm.T + np.array(X.t)     # world = s R l + t
+    spacing = X.s * 2 * h.max() / (m - 1)
+    rng = np.random.default_rng(13)
+    for p in rng.uniform(-1.5, 1.5, (120, 3)):
+        loc = Rm.T @ (p - np.array(X.t)) / X.s
+        inside = np.all(np.abs(loc) < h)
+        d = _sdf(prim, p)
+        assert (d < 0) == inside
+        assert abs(abs(d) - np.sqrt(((surf - p) ** 2).sum(1)).min()) <= spacing, p
+
+
+def test_quarter_turn_and_scale_identities():
+    # a quarter turn about z swaps the box's x and y half extents; a scaled
+    # sphere is the sphere of scaled radius
+    rng = np.random.default_rng(14)
+    qt = W.Prim(W.BOX, (0.0, 0.0, 0.0, 0.5, 0.2, 0.3), W.Xform(rot=W.rotation((0, 0, 1), 90.0), t=(0.1, 0.2, 0.3)))
+    swapped = W.Prim(W.BOX, (0.1, 0.2, 0.3, 0.2, 0.5, 0.3))
+    sc = W.Prim(W.SPHERE, (0.0, 0.0, 0.0, 0.4), W.Xform(t=(0.2, 0.0, -0.1), s=2.5))
+    big = W.Prim(W.SPHERE, (0.2, 0.0, -0.1, 1.0))
+    for p in rng.uniform(-2, 2, (100, 3)):
+        assert abs(_sdf(qt, p) - _sdf(swapped, p)) < 1e-12
+        assert abs(_sdf(sc, p) - _sdf(big, p)) < 1e-12
+
+
+def test_elongated_sphere_is_capsule():
+    # elongating a sphere of radius r by h along x gives the capsule on the
+    # segment [-h, h] x {0} x {0} of radius r (Fig. 1 o)
+    h, r = 0.35, 0.2
+    el = W.Prim(W.SPHERE, (0.0, 0.0, 0.0, r), W.Xform(t=(0.1, -0.2, 0.3), op=W.ELONGATE, a=(h, 0.0, 0.0, 0.0)))
+    cap = W.Prim(W.CAPSULE, (0.1 - h, -0.2, 0.3, 0.1 + h, -0.2, 0.3, r))
+    rng = np.random.default_rng(15)
+    for p in rng.uniform(-1.5, 1.5, (200, 3)):
+        assert abs(_sdf(el, p) - _sdf(cap, p)) < 1e-12
+
+
+def test_repetition_is_union_of_copies():
+    # repeating a centred sphere with periods (0.5, 0.7) and 2 copies each way
+    # equals the union of the 25 explicit spheres, everywhere (Fig. 1 i)
+    r, c = 0.15, (0.5, 0.7, 0.0)
+    rep = W.Prim(W.SPHERE, (0.0, 0.0, 0.0, r), W.Xform(t=(0.1, 0.0, 0.0), op=W.REPEAT, a=c + (2.0,)))
+    copies = [W.Prim(W.SPHERE, (0.1 + i * c[0], j * c[1], 0.0, r)) for i in range(-2, 3) for j in range(-2, 3)]
+    union = _one_region_scene(copies, W.prim_program(list(range(len(copies)))))
+    rng = np.random.default_rng(16)
+    for p in rng.uniform(-2.5, 2.5, (300, 3)):
+        assert abs(_sdf(rep, p) - O.region_sdf(union, 0, p)) < 1e-12
+
+
+def _membership_twist(p, h, k, bend=False):
+    # inside test written from the definition: rotate (x, y) by 2 pi k z
+    # (twist) or 2 pi k x (bend), then test the box
+    th = 2 * math.pi * k * (p[0] if bend else p[2])
+    x = math.cos(th) * p[0] - math.sin(th) * p[1]
+    y = math.sin(th) * p[0] + math.cos(th) * p[1]
+    return abs(x) < h[0] and abs(y) < h[1] and abs(p[2]) < h[2]
+
+
+@pytest.mark.parametrize("op", [W.TWIST, W.BEND])
+def test_twist_bend_sign_and_safe_bound(op):
+    # the twisted / bent box: negative exactly inside the deformed shape, and
+    # a safe sphere-tracing distance: no point of the ball of radius |d(p)|
+    # about p changes membership (the deformation stretches space, so the
+    # distance is divided by the map's stretch bound; Sec. 5 on non-bounded
+    # SDFs).  Membership is written from the definition, independently.
+    h = (0.5, 0.12, 0.4) if op == W.BEND else (0.15, 0.1, 0.6)
+    k = 0.3
+    rho = math.hypot(h[0], h[1])
+    prim = W.Prim(W.BOX, (0.0, 0.0, 0.0) + h, W.Xform(op=op, a=(k, rho, 0.0, 0.0)))
+    bend = op == W.BEND
+    rng = np.random.default_rng(17 if op == W.TWIST else 18)
+    pts = rng.uniform(-0.8, 0.8, (300, 3))
+    d = np.array([_sdf(prim, p) for p in pts])
+    for p, dv in zip(pts, d):
+        assert (dv < 0) == _membership_twist(p, h, k, bend), p
+    dirs = _fib_sphere(200)
+    tight = 0
+    for p, dv in zip(pts[:150], d[:150]):
+        inside = dv < 0
+        for f in (0.5, 0.999999):
+            for q in p + f * abs(dv) * dirs:
+                assert _membership_twist(q, h, k, bend) == inside, (p, dv, q)
+        # not vacuous: a ball a few times larger reaches the other side
+        tight += any(_membership_twist(q, h, k, bend) != inside for q in p + 3.0 * abs(dv) * dirs)
+    assert tight > 100
+
+
+def test_rotated_scaled_slab_beer_lambert():
+    # transport through a placed primitive: a non-scattering, index-matched
+    # slab of local thickness 0.5, scaled by 1.4 and tilted 30 degrees, with
+    # the beam along its normal: T = exp(-mu * 0.7)
+    mu, n = 1.1, 40000
+    Rm = W.rotation((1.0, 0.0, 0.0), 30.0)
+    slab = W.Prim(W.BOX, (0.0, 0.0, 0.0, 3.0, 3.0, 0.25), W.Xform(rot=Rm, t=(0.0, 0.0, -1.0), s=1.4))
+    sc = W.Scene((slab,), (W.Region(W.prim_program([0]), mu, 0.0, 0.0, 1.0),), 1.0, (-4, -4, -4), (4, 4, 4))
+    nrm = np.array(Rm).reshape(3, 3) @ np.array([0.0, 0.0, 1.0])
+    start = np.array([0.0, 0.0, -1.0]) + 1.5 * nrm
+    _, tot, _ = _run(sc, W.Source(W.PENCIL, tuple(start), tuple(-nrm)), n, 23, fluence=False)
+    assert _within(_frac(tot, "T"), math.exp(-mu * 0.7), n)
+    assert tot["fresnel"] == 0
+
+
+def test_gallery_energy_and_segment_safety():
+    wl = W.sdf_gallery(400, grid_n=20)
+    _, tot, rec = O.run(wl, records=True)
+    pb = rec["R"] + rec["T"] + rec["A"] + rec["killed"] - rec["gain"]
+    assert np.all(np.abs(pb - FX) <= 0.5 * (rec["scatters"] + 3) + 1)
+    assert tot["fresnel"] > 0 and tot["max_steps_hit"] == 0
+    # the same transport with segment stepping: identical physics, R/T/A agree
+    _, ts, _ = O.run(wl.with_stepping(W.SEGMENT).with_packets(4000), 10_000, 14_000)
+    _, tp, _ = O.run(wl.with_packets(4000), 20_000, 24_000)
+    for key in ("R", "T", "A"):
+        assert abs(_frac(ts, key) - _frac(tp, key)) < 5 * math.sqrt(0.25 / 4000) * 1.5
+
+
 
 def test_scene_eval_region_priority_and_dmin():
     # two nested regions: later index wins where both contain p
@@ -669,6 +845,7 @@ SEGMENT_SCENES = {
     "slab": lambda: W.three_layer_slab().scene,
     "glass": lambda: W.glass_container().scene,
     "vessel": lambda: W.vessel_network().scene,
+    "gallery": lambda: W.sdf_gallery().scene,
 }
 
 
@@ -797,3 +974,4 @@ def test_segment_stepping_same_transport_fewer_steps(factory):
     pb = r1["R"] + r1["T"] + r1["A"] + r1["killed"] - r1["gain"]
     assert np.all(np.abs(pb - FX) <= 0.5 * (r1["scatters"] + 3) + 1)
     assert t1["steps"] < 0.7 * t0["steps"]
+

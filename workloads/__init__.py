@@ -14,12 +14,15 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-# Primitive kinds (Sec. 2.2, Eq. 2-3; box and capsule used in Sec. 4).
-SPHERE, BOX, CAPSULE = "sphere", "box", "capsule"
+# Primitive kinds (Sec. 2.2, Eq. 2-3; box and capsule used in Sec. 4; torus
+# and capped cylinder among the basic shapes of the Fig. 1 gallery).
+SPHERE, BOX, CAPSULE, TORUS, CYLINDER = "sphere", "box", "capsule", "torus", "cylinder"
+# Domain operations of a primitive's frame (Sec. 2.2, Fig. 1 i, o, p, q).
+XF_NONE, ELONGATE, TWIST, BEND, REPEAT = "none", "elongate", "twist", "bend", "repeat"
 # CSG node kinds (Sec. 2.2, Fig. 1 e-h).  'prim' pushes a primitive.
 PRIM, UNION, SMOOTH_UNION, INTERSECT, SUBTRACT = (
     "prim", "union", "smooth_union", "intersect", "subtract")
@@ -31,11 +34,41 @@ SPHERE_TRACING, SEGMENT = "sphere_tracing", "segment"
 
 
 @dataclass(frozen=True)
+class Xform:
+    """Frame of a primitive: a point with local coordinates l sits at
+    s R l + t (R row-major, orthonormal).  op acts on the local point:
+    elongate (a[0..2] half lengths), twist about local z / bend in the local
+    x-y plane (a[0] turns per unit length, a[1] the radius the shape reaches
+    from the axis), repeat (a[0..2] periods, 0 = none; a[3] copies each
+    way)."""
+    rot: Tuple[float, ...] = (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)
+    t: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    s: float = 1.0
+    op: str = XF_NONE
+    a: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)
+
+
+def rotation(axis: Sequence[float], degrees: float) -> Tuple[float, ...]:
+    """Row-major rotation matrix about a unit axis (Rodrigues' formula)."""
+    x, y, z = (float(v) for v in axis)
+    n = math.sqrt(x * x + y * y + z * z)
+    x, y, z = x / n, y / n, z / n
+    th = math.radians(degrees)
+    c, s, C1 = math.cos(th), math.sin(th), 1.0 - math.cos(th)
+    return (c + x * x * C1, x * y * C1 - z * s, x * z * C1 + y * s,
+            y * x * C1 + z * s, c + y * y * C1, y * z * C1 - x * s,
+            z * x * C1 - y * s, z * y * C1 + x * s, c + z * z * C1)
+
+
+@dataclass(frozen=True)
 class Prim:
     """sphere: (cx, cy, cz, r); box: (cx, cy, cz, hx, hy, hz);
-    capsule: (ax, ay, az, bx, by, bz, r)."""
+    capsule: (ax, ay, az, bx, by, bz, r); torus: (cx, cy, cz, R, r) about
+    the z axis; cylinder: (cx, cy, cz, r, half height) along z.  With a
+    frame the parameters are local coordinates."""
     kind: str
     params: Tuple[float, ...]
+    xform: Optional[Xform] = None
 
 
 @dataclass(frozen=True)
@@ -360,6 +393,40 @@ def iso_sphere(tau: float = 100.0, npackets: int = 1_000_000, seed: int = 7, pre
                     Source(ISO_POINT, (0.0, 0.0, 0.0), (0.0, 0.0, -1.0)),
                     Grid((-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), (grid_n, grid_n, grid_n)),
                     npackets, seed, precision)
+
+
+def sdf_gallery(npackets: int = 1_000_000, seed: int = 8, precision: str = "mixed",
+                grid_n: int = 100) -> Workload:
+    """The shapes and operations of the Fig. 1 gallery in one transport scene
+    (Sec. 2.2): a tissue block z in [-2, 0] holding a tilted torus, a box
+    rotated about an oblique axis, a twisted bar, a bent bar, an elongated
+    sphere, a 5 x 5 array of repeated spheres (index-matched) and a capped
+    cylinder scaled by 1.5, each its own region with its own optics and
+    refractive index; disc beam r = 1.5 cm from above."""
+    prims = (
+        Prim(BOX, (0.0, 0.0, -1.0, 2.0, 2.0, 1.0)),
+        Prim(TORUS, (0.0, 0.0, 0.0, 0.5, 0.15), Xform(rot=rotation((1, 0, 0), 45.0), t=(-1.0, -1.0, -1.0))),
+        Prim(BOX, (0.0, 0.0, 0.0, 0.4, 0.2, 0.2), Xform(rot=rotation((1, 1, 1), 30.0), t=(1.0, -1.0, -1.0))),
+        Prim(BOX, (0.0, 0.0, 0.0, 0.15, 0.15, 0.5),
+             Xform(t=(-1.0, 1.0, -1.0), op=TWIST, a=(0.25, 0.2122, 0.0, 0.0))),
+        Prim(BOX, (0.0, 0.0, 0.0, 0.6, 0.1, 0.1), Xform(t=(1.0, 1.0, -1.0), op=BEND, a=(0.15, 0.61, 0.0, 0.0))),
+        Prim(SPHERE, (0.0, 0.0, 0.0, 0.1), Xform(t=(0.0, 0.0, -0.5), op=ELONGATE, a=(0.3, 0.0, 0.0, 0.0))),
+        Prim(SPHERE, (0.0, 0.0, 0.0, 0.08), Xform(t=(0.0, 0.0, -1.6), op=REPEAT, a=(0.3, 0.3, 0.0, 2.0))),
+        Prim(CYLINDER, (0.0, 0.0, 0.0, 0.2, 0.25), Xform(t=(0.0, 0.0, -1.0), s=1.5)),
+    )
+    regions = (
+        Region(prim_program([0]), 0.2, 20.0, 0.8, 1.37),
+        Region(prim_program([1]), 1.0, 50.0, 0.9, 1.45),
+        Region(prim_program([2]), 0.5, 10.0, 0.8, 1.5),
+        Region(prim_program([3]), 2.0, 30.0, 0.9, 1.4),
+        Region(prim_program([4]), 0.3, 5.0, 0.7, 1.33),
+        Region(prim_program([5]), 5.0, 100.0, 0.95, 1.4),
+        Region(prim_program([6]), 3.0, 60.0, 0.9, 1.37),
+        Region(prim_program([7]), 0.1, 2.0, 0.5, 1.55),
+    )
+    scene = Scene(prims, regions, 1.0, (-2.1, -2.1, -2.1), (2.1, 2.1, 0.2))
+    return Workload(f"sdf_gallery_{grid_n}c", scene, Source(DISC, (0.0, 0.0, 0.1), (0.0, 0.0, -1.0), 1.5),
+                    Grid((-2.0, -2.0, -2.0), (2.0, 2.0, 0.0), (grid_n, grid_n, grid_n)), npackets, seed, precision)
 
 
 def all_configs():
