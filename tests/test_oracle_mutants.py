@@ -58,18 +58,29 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_mutant(tmp_path, name, old, new):
+def _run_mutant(tmp, name, old, new):
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site not unique/found: {name}"
-    mpath = tmp_path / "mutant.c"
-    mpath.write_text(src.replace(old, new))
-    lib = tmp_path / "libmutant.so"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(mpath),
-                           "-o", str(lib), "-lm"])
-    env = dict(os.environ, ORACLE_LIB=str(lib))
+    if src.count(old) != 1:
+        return name, f"mutation site not unique/found"
+    mpath = os.path.join(tmp, f"{name}.c")
+    with open(mpath, "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(tmp, f"lib{name}.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", mpath,
+                           "-o", lib, "-lm"])
+    env = dict(os.environ, ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return name, None if r.returncode != 0 else f"no pin caught it:\n{r.stdout[-1500:]}"
+
+
+@pytest.mark.slow
+def test_pins_catch_every_mutant(tmp_path):
+    # the mutants run side by side, one pin-suite process each
+    from concurrent.futures import ThreadPoolExecutor
+    workers = max(2, min(len(MUTANTS), os.cpu_count() or 2))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda m: _run_mutant(str(tmp_path), *m), MUTANTS))
+    missed = [(n, why) for n, why in results if why]
+    assert not missed, missed

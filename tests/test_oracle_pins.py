@@ -860,7 +860,7 @@ def test_segment_step_never_reaches_a_surface(name):
     rng = np.random.default_rng(hash(name) % 2**32)
     lo, hi = np.array(sc.bbox_lo), np.array(sc.bbox_hi)
     checked = longer = 0
-    for _ in range(150):
+    for _ in range(90):
         p = lo + (hi - lo) * rng.random(3)
         u = rng.normal(size=3)
         u /= np.linalg.norm(u)
@@ -871,14 +871,14 @@ def test_segment_step_never_reaches_a_surface(name):
         assert t >= e["dmin"] - dh
         longer += t > e["dmin"] - dh + 1e-12
         signs = [np.sign(O.region_sdf(sc, r, p)) for r in range(len(sc.regions))]
-        for s in np.linspace(0.0, t, 300):
+        for s in np.linspace(0.0, t, 160):
             q = p + s * u
             eq = O.scene_eval(sc, q)
             assert eq["dmin"] >= dh - 1e-12, (name, p, u, t, s, eq)   # rounding of |p - c| - r
             assert eq["dbox"] < 0
             assert [np.sign(O.region_sdf(sc, r, q)) for r in range(len(sc.regions))] == signs
         checked += 1
-    assert checked > 30 and longer > checked // 4
+    assert checked > 20 and longer > checked // 4
 
 
 def test_segment_step_exact_for_planes_and_spheres():
@@ -974,4 +974,3 @@ def test_segment_stepping_same_transport_fewer_steps(factory):
     pb = r1["R"] + r1["T"] + r1["A"] + r1["killed"] - r1["gain"]
     assert np.all(np.abs(pb - FX) <= 0.5 * (r1["scatters"] + 3) + 1)
     assert t1["steps"] < 0.7 * t0["steps"]
-
