@@ -80,9 +80,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the packet kernel from the committed ncu
-    summary, or None when the kernel source changed after that capture."""
+def recorded_traffic(key: str = "dram_bytes_per_launch"):
+    """A figure of the committed ncu summary of the packet kernel (DRAM bytes
+    per launch, or thread instructions per packet), or None when the kernel
+    source changed after that capture."""
     path = os.path.join(ROOT, TRAFFIC_SUMMARY)
     if not os.path.exists(path):
         return None
@@ -96,7 +97,7 @@ def recorded_traffic():
     if vals.get("kernel_source_sha256") != kernel_source_hash():
         return None
     try:
-        return int(vals["dram_bytes_per_launch"])
+        return int(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -430,6 +431,16 @@ def main():
                        "kernel": f"packets_{args.precision}",
                        "algorithmic_flops_per_packet": flops / args.packets,
                        "atomics_per_s": totals_mixed["pieces"] / kernel_s}
+    # lane-issue view: executed thread instructions (ncu, per packet) against
+    # the issue ceiling of 152 SMs x 4 schedulers x 32 lanes x clock
+    tipp = recorded_traffic("thread_instructions_per_packet") if args.stepping == W.SEGMENT else None
+    if tipp:
+        issue_peak = sm_count * 4 * 32 * mhz * 1e6
+        out["issue_utilisation"] = {"thread_instructions_per_packet": tipp,
+                                    "achieved_per_s": tipp * args.packets / kernel_s, "peak_per_s": issue_peak,
+                                    "frac": tipp * args.packets / kernel_s / issue_peak,
+                                    "note": "thread instructions per packet from the ncu summary in profiles/ "
+                                            "(2e5-packet capture of this kernel source)"}
     out["counters_per_packet"] = {k: totals_mixed[k] / args.packets for k in
                                   ("steps", "scene_evals", "scatters", "interfaces", "fresnel", "pieces")}
     out["counters_per_packet"]["refined_fraction_of_fresnel"] = (
