@@ -530,9 +530,12 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     for (int i = 0; i < np; ++i) H.general = H.general || !plain_prim(sc->prims[i]);
     {   // analytic normals when every region's program is short and made of
         // spheres, boxes and capsules in scene coordinates
+        // (the culled region counts as short: its gradient folds over the
+        // cell's few candidates)
         int longest = 0;
         bool plain = true;
-        for (int r = 0; r < nr; ++r) longest = std::max(longest, rr[r].y - rr[r].x);
+        for (int r = 0; r < nr; ++r)
+            if (r != cg.region) longest = std::max(longest, rr[r].y - rr[r].x);
         for (int i = 0; i < np; ++i) plain = plain && plain_prim(sc->prims[i]);
         H.analytic_nrm = longest <= kAnalyticNormalMaxInstr && plain ? 1 : 0;
     }

@@ -330,8 +330,12 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             } else if (phase == kNear) {
                 rnear = E.region;
                 if (region_n32(S, rnear) == region_n32(S, rfar)) {
-                    const float e = 2.f * delta * sg;
-                    px = qx + e * nx; py = qy + e * ny; pz = qz + e * nz;
+                    // matched indices: cross on the ray, as a Fresnel landing
+                    // does.  A push along n alone never advances along u, and
+                    // where the normal turns between the two sides (a smooth
+                    // union's crease) a packet moving along the wall was
+                    // pushed back and forth across it until the step cap.
+                    land32(qx, qy, qz, ux, uy, uz, nx, ny, nz, 2.f * delta, sg, px, py, pz);
                     phase = kTrace;
                     iter_done = true;
                 } else {

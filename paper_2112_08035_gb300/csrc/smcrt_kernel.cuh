@@ -549,9 +549,39 @@ __device__ __forceinline__ void csg_grad32(int op, float &a, float &ax, float &a
 
 // Value and gradient of one surface's SDF (region program, or the bounding
 // box for r = -1): used for analytic normals on short programs.
+// Value and gradient of the culled region (the fold of union / smooth union
+// over the cell's candidates, as culled_region32): the gradient of a smooth
+// minimum is the h-weighted blend of its operands' gradients.  Only called
+// within delta of the region's surface, where the fold is below the clamp.
+__device__ __forceinline__ float grad_culled32(const DevScene &S, float x, float y, float z, float &gx, float &gy,
+                                               float &gz)
+{
+    gx = gy = gz = 0.f;
+    const int g = S.cull_g;
+    const int cx = __float2int_rd((x - S.cull_lo[0]) * S.cull_inv_s[0]);
+    const int cy = __float2int_rd((y - S.cull_lo[1]) * S.cull_inv_s[1]);
+    const int cz = __float2int_rd((z - S.cull_lo[2]) * S.cull_inv_s[2]);
+    if ((unsigned)cx >= (unsigned)g || (unsigned)cy >= (unsigned)g || (unsigned)cz >= (unsigned)g)
+        return S.cull_rmax;
+    const int c = (cz * g + cy) * g + cx;
+    const int o0 = __ldg(S.cull_off + c), o1 = __ldg(S.cull_off + c + 1);
+    if (o1 <= o0) return S.cull_rmax;
+    int i = __ldg(S.cull_list + o0);
+    float acc = prim_grad32(S, __ldg(S.pkind + i), i, x, y, z, gx, gy, gz);
+    for (int j = o0 + 1; j < o1; ++j) {
+        i = __ldg(S.cull_list + j);
+        float bx, by, bz;
+        const float b = prim_grad32(S, __ldg(S.pkind + i), i, x, y, z, bx, by, bz);
+        csg_grad32(S.cull_op, acc, gx, gy, gz, b, bx, by, bz, S.cull_kinv);
+    }
+    if (!(acc < S.cull_rmax)) { gx = gy = gz = 0.f; return S.cull_rmax; }
+    return acc;
+}
+
 static __device__ __noinline__ float grad_surface32(const DevScene &S, int r, float x, float y, float z, float &gx,
                                              float &gy, float &gz)
 {
+    if (r >= 0 && r == S.cull_region) return grad_culled32(S, x, y, z, gx, gy, gz);
     if (r < 0) {
         const float px = x - S.bbc32[0], py = y - S.bbc32[1], pz = z - S.bbc32[2];
         const float qx = fabsf(px) - S.bbh32[0], qy = fabsf(py) - S.bbh32[1], qz = fabsf(pz) - S.bbh32[2];
