@@ -68,12 +68,13 @@ struct Rng {
 
 // Uniforms in (0, 1]: FP64 uses the whole 32-bit word, FP32 its top 24 bits.
 __device__ __forceinline__ double u01_64(uint32_t w) { return ((double)w + 1.0) * (1.0 / 4294967296.0); }
-// FP32: the top 24 bits mapped to bin midpoints, (k + 1/2) 2^-24, strictly
-// inside (0, 1) and unbiased.  The value 1 would put a square or disc
-// source's packet exactly on the boundary of its footprint: where that edge
-// lies in a scene face, such a packet crawled along the face at distance 0
-// (moving exactly parallel to it) until the step cap.
-__device__ __forceinline__ float u01_32(uint32_t w) { return ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f); }
+// FP32: the top 23 bits mapped to bin midpoints, (k + 1/2) 2^-23, strictly
+// inside (0, 1) and unbiased (24 bits would not do: (2^24 - 1/2) 2^-24
+// rounds to 1 in FP32).  The value 1 would put a square or disc source's
+// packet exactly on the boundary of its footprint: where that edge lies in
+// a scene face, such a packet crawled along the face at distance 0 (moving
+// exactly parallel to it) until the step cap.
+__device__ __forceinline__ float u01_32(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
 
 // ---------------------------------------------------------------------------
 // FP64 ln and sin/cos(2 pi t), written from the series (not libdevice):
