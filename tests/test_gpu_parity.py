@@ -191,6 +191,20 @@ def test_mixed_glass_shell_traps_no_packet(ctx, stepping):
     assert t["max_steps_hit"] == 0, t["max_steps_hit"]
 
 
+def test_mixed_vessel_served_job_no_step_cap(ctx):
+    # a vessel job of the served mix (2.4e6 packets, 64 capsules in a smooth
+    # union) once had five packets at the step cap: two launched exactly on
+    # the tissue box's face by an FP32 uniform of 1 and crawling along it at
+    # distance 0, three pushed back and forth across a capsule wall at a
+    # smooth-union crease by matched-index crossings that did not advance
+    # along the ray
+    wl = W.served_mix(40, 4, stepping=W.SEGMENT)[35]
+    assert wl.name.endswith("vessel") and wl.npackets > 2_000_000
+    _, t = run_gpu(ctx, wl, "mixed")
+    assert t["packets"] == wl.npackets
+    assert t["max_steps_hit"] == 0, t["max_steps_hit"]
+
+
 def test_register_variants_identical(ctx):
     # the register budget changes occupancy, never arithmetic
     wl = W.glass_container(700, grid_n=32)
