@@ -419,23 +419,31 @@ def main():
     peaks, src = load_peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = out["clocks"]["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1455.0
-    peak_tflops = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    nominal_tflops = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    # measured ceilings: the library's FMA and int64-atomic microbenchmarks
+    mb = smc.microbench(local)
+    peak_tflops = mb["fp32_flops"] / 1e12
     flops = three_layer_flops(totals_mixed)
     achieved = flops / kernel_s / 1e12
+    atomics = totals_mixed["pieces"] / kernel_s
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                        "frac": achieved / peak_tflops, "traffic": recorded_traffic(),
                        "traffic_note": "DRAM bytes per full-size launch from the ncu summary in profiles/ "
                                        "(null if the kernel changed since)",
-                       "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 (FMA) x {mhz:.0f} MHz "
-                                     f"(median SM clock sampled under load)",
+                       "peak_basis": "measured: smcrt_microbench FP32 FMA kernel on this GPU "
+                                     f"(nominal {sm_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz = "
+                                     f"{nominal_tflops:.1f} TFLOP/s)",
                        "kernel": f"packets_{args.precision}",
                        "algorithmic_flops_per_packet": flops / args.packets,
-                       "atomics_per_s": totals_mixed["pieces"] / kernel_s}
+                       "atomics_per_s": atomics,
+                       "atomics_peak_distinct_per_s": mb["atomics_distinct_per_s"],
+                       "atomics_peak_hot_per_s": mb["atomics_hot_per_s"],
+                       "atomics_frac": atomics / mb["atomics_distinct_per_s"]}
     # lane-issue view: executed thread instructions (ncu, per packet) against
     # the issue ceiling of 152 SMs x 4 schedulers x 32 lanes x clock
     tipp = recorded_traffic("thread_instructions_per_packet") if args.stepping == W.SEGMENT else None
     if tipp:
-        issue_peak = sm_count * 4 * 32 * mhz * 1e6
+        issue_peak = sm_count * 4 * 32 * mhz * 1e6   # lane-issue slots per second at the sampled clock
         out["issue_utilisation"] = {"thread_instructions_per_packet": tipp,
                                     "achieved_per_s": tipp * args.packets / kernel_s, "peak_per_s": issue_peak,
                                     "frac": tipp * args.packets / kernel_s / issue_peak,

@@ -372,6 +372,19 @@ int smcrt_cancel(smcrt_ctx *ctx, uint64_t job_id);
 /* Serving counters: jobs queued, running, launches issued so far. */
 int smcrt_serving_stats(smcrt_ctx *ctx, int64_t *queued, int64_t *running, int64_t *launches);
 
+/* Measured ceilings of this GPU for the packet kernel's roofline (the paper
+ * has no counterpart; Sec. 3.2 reports CPU timings only):
+ *   fp32_flops        FP32 FMA throughput (an FMA counts 2 flops) of a
+ *                     kernel of eight independent FMA chains per thread;
+ *   atomics_distinct  int64 atomic adds per second to scattered addresses
+ *                     of a 64 MiB table (the fluence tally's access);
+ *   atomics_hot       the same to 32 addresses (a beam's hottest voxels).
+ * scratch_dev: caller-owned device memory of at least 64 MiB, overwritten.
+ * Synchronous; runs on a private stream of `device`.  Returns
+ * SMCRT_ERR_BAD_ARG for null pointers or a smaller scratch. */
+int smcrt_microbench(int device, void *scratch_dev, size_t scratch_bytes, double *fp32_flops,
+                     double *atomics_distinct, double *atomics_hot);
+
 #ifdef __cplusplus
 }
 #endif

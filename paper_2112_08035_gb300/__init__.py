@@ -141,6 +141,8 @@ def lib():
                                                   C.POINTER(C.c_int64)]),
                 "smcrt_run_noalloc": (C.c_int, [C.POINTER(Scene), C.POINTER(Source), C.POINTER(Grid), u64, u64,
                                                 u64, i32, vp, vp, vp]),
+                "smcrt_microbench": (C.c_int, [C.c_int, vp, C.c_size_t, C.POINTER(C.c_double),
+                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -352,3 +354,14 @@ def totals_tensor(device="cuda"):
 def totals_from_tensor(t) -> dict:
     v = t.detach().cpu().numpy()
     return {f: int(v[i]) for i, f in enumerate(TOTAL_FIELDS)}
+
+
+def microbench(device: int = 0):
+    """Measured FP32 FMA flop/s and int64 atomic rates (distinct, hot) of
+    the GPU (smcrt_microbench); uses a 64 MiB torch scratch buffer."""
+    import torch
+    buf = torch.empty(1 << 23, dtype=torch.int64, device=f"cuda:{device}")
+    f, a, h = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().smcrt_microbench(int(device), _ptr(buf), buf.numel() * 8, C.byref(f), C.byref(a), C.byref(h)),
+           "microbench")
+    return {"fp32_flops": f.value, "atomics_distinct_per_s": a.value, "atomics_hot_per_s": h.value}

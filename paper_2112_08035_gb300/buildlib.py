@@ -31,6 +31,7 @@ UNITS = {
     "smcrt_k32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "smcrt_util.cu": [],
     "smcrt_noalloc.cu": [],
+    "smcrt_microbench.cu": [],
 }
 HEADERS = ["smcrt_internal.h", "smcrt_kernel.cuh"]
 
