@@ -104,6 +104,35 @@ def test_validation_rejects_corrupt_scenes():
         assert _bad(c) == smc.ERR_BAD_SCENE
 
 
+def test_validation_of_shapes_and_frames():
+    wl = W.sdf_gallery(10, grid_n=8)
+    assert smc.validate(wl) >= 1
+    sc = wl.scene
+
+    def with_prim(i, prim):
+        prims = list(sc.prims)
+        prims[i] = prim
+        return replace(wl, scene=replace(sc, prims=tuple(prims)))
+    tor, cyl, box = sc.prims[1], sc.prims[7], sc.prims[2]
+    X = box.xform
+    reflect = (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, -1.0)
+    skewed = (1.0, 0.1, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)
+    cases = [
+        with_prim(1, replace(tor, params=(0.0, 0.0, 0.0, 0.2, 0.3))),          # tube wider than the ring
+        with_prim(1, replace(tor, params=(0.0, 0.0, 0.0, 0.5, 0.0))),
+        with_prim(7, replace(cyl, params=(0.0, 0.0, 0.0, 0.2, -0.1))),
+        with_prim(2, replace(box, xform=replace(X, rot=reflect))),              # det -1
+        with_prim(2, replace(box, xform=replace(X, rot=skewed))),               # not orthonormal
+        with_prim(2, replace(box, xform=replace(X, s=0.0))),
+        with_prim(2, replace(box, xform=replace(X, s=float("inf")))),
+        with_prim(2, replace(box, xform=replace(X, op=W.REPEAT, a=(0.3, 0.3, 0.0, 1.5)))),   # fractional count
+        with_prim(2, replace(box, xform=replace(X, op=W.ELONGATE, a=(-0.1, 0.0, 0.0, 0.0)))),
+        with_prim(2, replace(box, xform=replace(X, op=W.TWIST, a=(0.2, -1.0, 0.0, 0.0)))),
+    ]
+    for c in cases:
+        assert _bad(c) == smc.ERR_BAD_SCENE
+
+
 def test_csg_stack_depth_limit():
     # n nested operands need n - 1 register slots (the last primitive fuses
     # with its operator): 5 compiles, 6 exceeds the 4-deep device stack
