@@ -280,15 +280,18 @@ int smcrt_plan_launch(smcrt_plan *plan, uint64_t id_begin, uint64_t npackets, ui
 /* Register budget of the packet kernel: variant 0, 1, 2 keep 5/4/3 (mixed)
  * or 4/3/2 (FP64) blocks of 128 threads resident per SM; fewer resident
  * blocks give each thread more registers (no spilling) at lower occupancy.
- * Results do not depend on the variant. */
+ * MIXED plans also take 3, 4, 5: the same budgets with each warp staging
+ * the scene's instruction stream and FP32 tables in shared memory (when
+ * they fit 4 KiB).  Results do not depend on the variant. */
 int smcrt_plan_set_variant(smcrt_plan *plan, int32_t variant);
 
 /* Read back the kernel's device error word for the plan's last launches
  * (0 = none) and clear it. */
 int smcrt_plan_status(smcrt_plan *plan, int32_t *status);
 
-/* Time the candidate launch shapes (register-budget variant x threads per
- * block x resident blocks) on a short trial run of this plan and keep the
+/* Time the candidate launch shapes (register-budget variant x, for MIXED
+ * plans, scene tables in global or shared memory x threads per block x
+ * resident blocks) on a short trial run of this plan and keep the
  * fastest; the choice is cached per scene shape in the context and applied
  * to later plans of the same shape.  Trial tallies go to scratch buffers.
  * *blocks / *threads / *variant (may be NULL) receive the choice. */

@@ -257,6 +257,7 @@ struct smcrt_plan {
     int ring = 64, ring_pos = 0;
     int *dstatus = nullptr;
     int blocks = 0, threads = 0, variant = 0;
+    int stage = 0;             // mixed: stage the scene tables in shared memory
     size_t cells = 0;
     size_t dbytes = 0;
     uint64_t shape_key = 0;
@@ -612,7 +613,8 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
         if (it != ctx->tuned.end()) {
             pl->blocks = it->second.blocks;
             pl->threads = it->second.threads;
-            pl->variant = it->second.variant;
+            pl->variant = it->second.variant % kNumVariants;
+            pl->stage = it->second.variant / kNumVariants;
         }
     }
     *out = pl.release();
@@ -642,6 +644,7 @@ int plan_launch_impl(smcrt_plan *pl, uint64_t id_begin, uint64_t n, uint64_t see
     jw.records = rec;
     jw.scene = pl->dscene;
     jw.cancelled = 0;
+    jw.stage = pl->precision == SMCRT_MIXED ? pl->stage : 0;
     JobWork *slot = pl->djobs + pl->ring_pos;
     pl->ring_pos = (pl->ring_pos + 1) % pl->ring;
     if (launch_set_job(slot, jw, s) != cudaSuccess) return SMCRT_ERR_CUDA;
@@ -974,6 +977,7 @@ void scheduler(smcrt_ctx *ctx)
             w.park_cycles = park_cycles;
             w.defer = j->ddefer;
             w.defer_in = (int32_t)(issued & 1);
+            w.stage = j->precision == SMCRT_MIXED ? 1 : 0;
             j->cursor += q;
             j->last_round = issued;
             if (j->precision == SMCRT_FP64) B.h_tab[kMaxSlots + nd++] = w;
@@ -1144,8 +1148,10 @@ int smcrt_plan_launch(smcrt_plan *pl, uint64_t id_begin, uint64_t npackets, uint
 
 int smcrt_plan_set_variant(smcrt_plan *pl, int32_t variant)
 {
-    if (!pl || variant < 0 || variant >= kNumVariants) return SMCRT_ERR_BAD_ARG;
-    pl->variant = variant;
+    const int nv = pl && pl->precision == SMCRT_MIXED ? 2 * kNumVariants : kNumVariants;
+    if (!pl || variant < 0 || variant >= nv) return SMCRT_ERR_BAD_ARG;
+    pl->variant = variant % kNumVariants;
+    pl->stage = variant / kNumVariants;
     return SMCRT_OK;
 }
 
@@ -1177,10 +1183,15 @@ int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int
     float best = 1e30f;
     int bb = 0, bt = 0, bv = 0;
     const int thread_opts[] = {64, 128};
-    const int saved_variant = pl->variant;
+    const int saved_variant = pl->variant, saved_stage = pl->stage;
     int rc = SMCRT_OK;
-    for (int v = 0; v < kNumVariants && rc == SMCRT_OK; ++v) {
+    // register variant x (mixed) scene tables read from global memory or
+    // staged in shared memory; public variant = register variant + 3 * stage
+    const int nv = pl->precision == SMCRT_MIXED ? 2 * kNumVariants : kNumVariants;
+    for (int pv = 0; pv < nv && rc == SMCRT_OK; ++pv) {
+        const int v = pv % kNumVariants;
         pl->variant = v;
+        pl->stage = pv / kNumVariants;
         for (int t : thread_opts) {
             const int occ = occupancy(pl->precision, t, v);
             if (occ < 1) continue;
@@ -1206,7 +1217,7 @@ int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int
                     best = ms_best;
                     bb = b;
                     bt = t;
-                    bv = v;
+                    bv = pv;
                 }
             }
         }
@@ -1217,11 +1228,13 @@ int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int
     cudaFree(tot);
     if (rc != SMCRT_OK) {
         pl->variant = saved_variant;
+        pl->stage = saved_stage;
         return rc;
     }
     pl->blocks = bb;
     pl->threads = bt;
-    pl->variant = bv;
+    pl->variant = bv % kNumVariants;
+    pl->stage = bv / kNumVariants;
     {
         std::lock_guard<std::mutex> lk(pl->ctx->tune_mu);
         pl->ctx->tuned[pl->shape_key] = {bb, bt, bv};

@@ -220,6 +220,8 @@ struct JobWork {
     int32_t defer_in;             // list resumed in this launch (0 / 1)
     JobDefer *defer;              // device, may be null (no parking)
     long long park_cycles;        // > 0: park a packet after this many SM cycles in the launch
+    int32_t stage;                // mixed kernel: stage the scene tables in shared memory
+    int32_t stage_pad;
 };
 
 // Kernel status word bits.

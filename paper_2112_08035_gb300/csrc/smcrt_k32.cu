@@ -76,7 +76,7 @@ __device__ __forceinline__ void scatter32(float &ux, float &uy, float &uz, float
 
 __device__ __forceinline__ float region_n32(const DevScene &S, int r)
 {
-    return r < 0 ? S.ambient_n32 : __ldg(S.reg32 + 2 * r + 1).x;
+    return r < 0 ? S.ambient_n32 : (*(S.reg32 + 2 * r + 1)).x;
 }
 
 __device__ __forceinline__ double region_n64(const DevScene &S, int r)
@@ -154,11 +154,46 @@ __device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, i
 }
 
 // Per-warp shared state: the staged scene and the warp's tally slots.
+// Scene-table staging (a launch option the autotuner tries): the warp copies
+// the instruction stream, primitive kinds, FP32 primitive and region tables
+// and region ranges of its job into shared memory when they fit here.
+constexpr int kStageBytes = 4096;
 struct WarpShared {
     DevScene S;
     WarpAcc acc;
     JobConst jc;
+    __align__(16) unsigned char tab[kStageBytes];
 };
+
+__device__ __forceinline__ void stage_tables(WarpShared *ws, int lane)
+{
+    DevScene &SS = ws->S;
+    const int ni = SS.ninstr, np = SS.nprims, nr = SS.nregions;
+    const int w_ins = 4 * ni, w_kind = np, w_p32 = 8 * np, w_r32 = 8 * nr, w_rr = 2 * nr;   // 4-byte words
+    const int o1 = 0, o2 = o1 + ((w_ins + 3) & ~3), o3 = o2 + ((w_kind + 3) & ~3), o4 = o3 + ((w_p32 + 3) & ~3),
+              o5 = o4 + ((w_r32 + 3) & ~3), end = o5 + w_rr;
+    if (end * 4 > kStageBytes) return;
+    uint32_t *T = reinterpret_cast<uint32_t *>(ws->tab);
+    const uint32_t *a = reinterpret_cast<const uint32_t *>(SS.instr);
+    for (int k = lane; k < w_ins; k += 32) T[o1 + k] = a[k];
+    a = reinterpret_cast<const uint32_t *>(SS.pkind);
+    for (int k = lane; k < w_kind; k += 32) T[o2 + k] = a[k];
+    a = reinterpret_cast<const uint32_t *>(SS.p32);
+    for (int k = lane; k < w_p32; k += 32) T[o3 + k] = a[k];
+    a = reinterpret_cast<const uint32_t *>(SS.reg32);
+    for (int k = lane; k < w_r32; k += 32) T[o4 + k] = a[k];
+    a = reinterpret_cast<const uint32_t *>(SS.rrange);
+    for (int k = lane; k < w_rr; k += 32) T[o5 + k] = a[k];
+    __syncwarp();
+    if (lane == 0) {
+        SS.instr = reinterpret_cast<const Instr *>(T + o1);
+        SS.pkind = reinterpret_cast<const int32_t *>(T + o2);
+        SS.p32 = reinterpret_cast<const float4 *>(T + o3);
+        SS.reg32 = reinterpret_cast<const float4 *>(T + o4);
+        SS.rrange = reinterpret_cast<const int2 *>(T + o5);
+    }
+    __syncwarp();
+}
 
 // One warp works through packet ids of job J until the job's cursor passes
 // its end.  Iteration structure (all lanes execute every stage; a lane's
@@ -376,7 +411,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         if (move) {
             float mu_t = 0.f, imu_t = 0.f;
             if (reg >= 0) {
-                const float4 RG = __ldg(S.reg32 + 2 * reg);
+                const float4 RG = (*(S.reg32 + 2 * reg));
                 mu_t = RG.x; imu_t = RG.y;
             }
             interact = mu_t > 0.f && tau < mu_t * L;
@@ -442,7 +477,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             phase = kTrace;
         }
         if (interact) {                            // implicit capture, HG, roulette
-            const float4 RG = __ldg(S.reg32 + 2 * reg);
+            const float4 RG = (*(S.reg32 + 2 * reg));
             const float wn = w * RG.z;
             pA += fx32(w - wn);
             w = wn;
@@ -583,6 +618,8 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
         const long long *s8 = reinterpret_cast<const long long *>(src);
         long long *d8 = reinterpret_cast<long long *>(&ws->S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+        __syncwarp();
+        if (J->stage) stage_tables(ws, lane);
         if (!G && ws->S.general) {           // a scene with general shapes needs the G instantiation
             if (lane == 0) atomicOr(status, kStatusBadJob);
             continue;

@@ -234,15 +234,32 @@ def test_register_variants_identical(ctx):
             for k in EXACT_KEYS:
                 assert got[1][k] == ref[1][k], (v, k)
         pm.close()
+    # mixed variants 3..5: the same budgets with the scene tables staged in
+    # each warp's shared memory -- the same numbers are loaded, so the same bits
+    torch = _torch()
+    for v in range(3, 6):
+        pm = ctx.plan(wl.with_packets(20000), "mixed")
+        pm.set_variant(v)
+        flu = torch.zeros((32, 32, 32), dtype=torch.int64, device="cuda")
+        tot = smc.totals_tensor()
+        pm.launch(0, 20000, wl.seed, flu, tot)
+        torch.cuda.synchronize()
+        assert np.array_equal(flu.cpu().numpy(), ref[0]), v
+        t = smc.totals_from_tensor(tot)
+        for k in EXACT_KEYS:
+            assert t[k] == ref[1][k], (v, k)
+        pm.close()
     with pytest.raises(smc.SmcrtError):
-        ctx.plan(wl, "mixed").set_variant(3)
+        ctx.plan(wl, "mixed").set_variant(6)
+    with pytest.raises(smc.SmcrtError):
+        ctx.plan(wl, "fp64").set_variant(3)
 
 
 def test_autotune_choice_is_valid(ctx):
     wl = W.three_layer_slab(50_000)
     plan = ctx.plan(wl, "mixed")
     blocks, threads, variant = plan.autotune(20_000)
-    assert blocks >= 152 and threads in (64, 128) and variant in (0, 1, 2)
+    assert blocks >= 152 and threads in (64, 128) and variant in range(6)
     fg, tg = run_gpu(ctx, wl, "mixed")   # a new plan of the same shape reuses the choice
     assert tg["packets"] == wl.npackets
     plan.close()
