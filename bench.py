@@ -410,7 +410,9 @@ def main():
                                   f"{args.stepping} stepping",
                       "stepping": args.stepping,
                       "packets_per_step": args.packets * world, "l2": "flushed between timed steps (256 MB write)",
-                      "launch": {"blocks": tuned[0], "threads": tuned[1], "register_variant": tuned[2],
+                      "launch": {"blocks": tuned[0], "threads": tuned[1], "variant": tuned[2],
+                                 "register_variant": tuned[2] % 3 if tuned[2] >= 0 else -1,
+                                 "scene_tables": "shared" if tuned[2] >= 3 else "global",
                                  "chosen_by": "smcrt_plan_autotune"}},
            "gpu_launches": 2 * args.steps,
            "clocks": clk.summary()}
