@@ -1,0 +1,123 @@
+"""The two 1e8-packet workloads at their full sizes, through the C-ABI.
+
+- Vessel network: 64 capsules in a smooth union inside a 5 mm tissue cube,
+  200^3 grid.
+- Glass container: a clear glass shell around a turbid liquid, 128^3 grid.
+
+Both runs use segment stepping, as the benchmark does.  The oracle cannot run
+1e8 packets, so the full-size results are checked in two ways.
+
+- FP64 kernel, on a random sample of the workload's packet ids: each
+  packet's record (R, T, A, killed, gain, scatters, steps) equals the
+  oracle's, one by one.
+- Mixed kernel, on all 1e8 packets:
+  - R/T/A agree with an independent oracle sample within 4 sigma of that
+    sample's error;
+  - the fluence map, summed over blocks of voxels, agrees with the sample's
+    map within the sample's own noise;
+  - energy closes;
+  - no packet reaches the step cap.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2112_08035_gb300 as smc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FX = 2.0 ** 32
+RECORD_KEYS = ("R", "T", "A", "killed", "gain", "scatters", "steps")
+
+# (workload, voxel block side for the coarse map, oracle sample size)
+CASES = [
+    ("vessel_network", lambda: W.vessel_network(), 10, 20000),
+    ("glass_container", lambda: W.glass_container(), 8, 40000),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = smc.Context(0)
+    yield c
+    c.close()
+
+
+def _coarse(f, b):
+    nz, ny, nx = f.shape
+    return f.reshape(nz // b, b, ny // b, b, nx // b, b).sum(axis=(1, 3, 5))
+
+
+@pytest.mark.parametrize("name,make,block,nsample", CASES, ids=[c[0] for c in CASES])
+def test_fp64_sampled_packets_full_size(ctx, name, make, block, nsample):
+    import torch
+    wl = make().with_stepping(W.SEGMENT)
+    g = wl.grid
+    plan = ctx.plan(wl, "fp64")
+    flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
+    tot = smc.totals_tensor()
+    rec = torch.zeros(8, dtype=torch.int64, device="cuda")
+    rng = np.random.default_rng(11)
+    ids = np.sort(rng.choice(wl.npackets, 300, replace=False))
+    try:
+        for i in ids:
+            rec.zero_()
+            plan.launch(int(i), 1, wl.seed, flu, tot, rec)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            rg = rec.cpu().numpy().view(smc.RECORD_DTYPE)[0]
+            _, _, ro = O.run(wl, int(i), int(i) + 1, threads=1, fluence=False, records=True)
+            for k in RECORD_KEYS:
+                assert rg[k] == ro[k][0], (name, int(i), k, rg[k], ro[k][0])
+    finally:
+        plan.close()
+    assert smc.totals_from_tensor(tot)["packets"] == len(ids)
+
+
+@pytest.mark.parametrize("name,make,block,nsample", CASES, ids=[c[0] for c in CASES])
+def test_mixed_full_size_against_oracle_sample(ctx, name, make, block, nsample):
+    import torch
+    wl = make().with_stepping(W.SEGMENT)
+    N = wl.npackets
+    g = wl.grid
+    plan = ctx.plan(wl, "mixed")
+    flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
+    tot = smc.totals_tensor()
+    plan.launch(0, N, wl.seed, flu, tot)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    plan.close()
+    t = smc.totals_from_tensor(tot)
+    fg = flu.cpu().numpy()
+    del flu
+    torch.cuda.empty_cache()
+    assert t["packets"] == N
+    assert t["max_steps_hit"] == 0, t["max_steps_hit"]
+    bal = (t["R"] + t["T"] + t["A"] + t["killed"] - t["gain"]) / FX
+    assert abs(bal - N) < 1e-4 * N, (bal, N)
+    assert fg.min() >= 0
+
+    # independent oracle sample: packet ids far from the GPU's [0, N), in
+    # two halves whose difference measures the sample's own noise
+    h = nsample // 2
+    base = 4 * N
+    fo1, _, r1 = O.run(wl.with_packets(h), base, records=True)
+    fo2, _, r2 = O.run(wl.with_packets(h), base + h, records=True)
+    ro = np.concatenate([r1, r2])
+    for k in ("R", "T", "A"):
+        x = ro[k].astype(np.float64) / FX
+        se = math.sqrt(x.var() / x.size * (1.0 + x.size / N))
+        z = abs(t[k] / FX / N - x.mean()) / max(se, 1e-12)
+        assert z < 4.0, (name, k, t[k] / FX / N, x.mean(), se, z)
+
+    cg = _coarse(fg, block) / FX / N
+    c1 = _coarse(fo1, block) / FX / h
+    c2 = _coarse(fo2, block) / FX / h
+    co = 0.5 * (c1 + c2)
+    # the sample of nsample packets has about 1/sqrt(2) of one half's noise
+    noise = np.linalg.norm(c1 - c2) / math.sqrt(2) / np.linalg.norm(co) / math.sqrt(2)
+    l2 = np.linalg.norm(cg - co) / np.linalg.norm(co)
+    assert l2 < 3.0 * noise + 1e-3, (name, l2, noise)
