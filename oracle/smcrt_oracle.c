@@ -693,6 +693,95 @@ static double segment_box(const double c[3], const double h[3], double d, const 
     return tf > 0.0 ? tf : 0.0;          /* inside: exit of the shrunk box */
 }
 
+/* Interval [t0, t1] of the ray p + t u inside the ball of radius rr whose
+ * centre is at p - o (t0 > t1: missed).  The far root of a quadratic comes
+ * from the near one through the product of the roots (no cancellation). */
+static void ray_ball(double ox, double oy, double oz, double rr, const double u[3], double *t0, double *t1)
+{
+    double b = ox * u[0] + oy * u[1] + oz * u[2];
+    double cc = ox * ox + oy * oy + oz * oz - rr * rr;
+    double disc = b * b - cc;
+    *t0 = INFINITY; *t1 = -INFINITY;
+    if (disc < 0.0) return;
+    double sq = sqrt(disc);
+    if (b > 0.0) {
+        double q = -(b + sq);
+        *t0 = q; *t1 = cc / q;
+    } else {
+        double q = sq - b;
+        if (q > 0.0) { *t1 = q; *t0 = cc / q; }
+        else { *t0 = 0.0; *t1 = 0.0; }
+    }
+}
+
+/* Interval of the ray inside the cylinder of radius rr about the axis a + s ba,
+ * between the planes s = 0 and s = 1 (o = p - a, L2 = |ba|^2).  The parts of
+ * o and u across the axis are formed first, so a ray nearly parallel to the
+ * axis keeps its small cross-axis motion accurate. */
+static void ray_cylinder(double ox, double oy, double oz, double bax, double bay, double baz, double L2,
+                         double rr, const double u[3], double *t0, double *t1)
+{
+    double uw = u[0] * bax + u[1] * bay + u[2] * baz;
+    double ow = ox * bax + oy * bay + oz * baz;
+    double lo = -INFINITY, hi = INFINITY;
+    *t0 = INFINITY; *t1 = -INFINITY;
+    if (uw != 0.0) {                     /* between the end planes */
+        double s0 = -ow / uw, s1 = (L2 - ow) / uw;
+        lo = fmin(s0, s1); hi = fmax(s0, s1);
+    } else if (ow < 0.0 || ow > L2) {
+        return;
+    }
+    double k = uw / L2, m = ow / L2;
+    double vx = u[0] - k * bax, vy = u[1] - k * bay, vz = u[2] - k * baz;
+    double wx = ox - m * bax, wy = oy - m * bay, wz = oz - m * baz;
+    double A = vx * vx + vy * vy + vz * vz;
+    double B = wx * vx + wy * vy + wz * vz;
+    double C = wx * wx + wy * wy + wz * wz - rr * rr;
+    if (A > 0.0) {                       /* A t^2 + 2 B t + C <= 0 */
+        double disc = B * B - A * C;
+        if (disc < 0.0) return;
+        double sq = sqrt(disc), c0, c1;
+        if (B > 0.0) {
+            double q = -(B + sq);
+            c0 = q / A; c1 = C / q;
+        } else {
+            double q = sq - B;
+            if (q > 0.0) { c1 = q / A; c0 = C / q; }
+            else { c0 = 0.0; c1 = 0.0; }
+        }
+        lo = fmax(lo, c0); hi = fmin(hi, c1);
+    } else if (C > 0.0) {
+        return;
+    }
+    *t0 = lo; *t1 = hi;
+}
+
+/* Capsule (convex: the cylinder between its end planes and the two end
+ * balls): from outside, the earliest entry of a part of the capsule grown by
+ * dh; from inside, the latest exit from a part of the capsule shrunk by dh. */
+static double segment_capsule(const double *q, double d, const double p[3], const double u[3], double dh)
+{
+    double rr = d > 0.0 ? q[6] + dh : q[6] - dh;
+    double ox = p[0] - q[0], oy = p[1] - q[1], oz = p[2] - q[2];
+    double bax = q[3] - q[0], bay = q[4] - q[1], baz = q[5] - q[2];
+    double L2 = bax * bax + bay * bay + baz * baz;
+    double t0[3], t1[3];
+    ray_ball(ox, oy, oz, rr, u, &t0[0], &t1[0]);
+    ray_ball(ox - bax, oy - bay, oz - baz, rr, u, &t0[1], &t1[1]);
+    ray_cylinder(ox, oy, oz, bax, bay, baz, L2, rr, u, &t0[2], &t1[2]);
+    double t;
+    if (d > 0.0) {
+        t = INFINITY;
+        for (int k = 0; k < 3; ++k)
+            if (t0[k] <= t1[k] && t1[k] >= 0.0) t = fmin(t, t0[k]);
+    } else {
+        t = 0.0;
+        for (int k = 0; k < 3; ++k)
+            if (t0[k] <= t1[k]) t = fmax(t, t1[k]);
+    }
+    return t > 0.0 ? t : 0.0;
+}
+
 static double segment_prim(const or_scene *S, const or_prim *pr, const double p[3], const double u[3],
                            double dh)
 {
@@ -700,6 +789,7 @@ static double segment_prim(const or_scene *S, const or_prim *pr, const double p[
     if (!(fabs(d) > dh)) return 0.0;
     if (pr->xform == 0 && pr->kind == 0) return segment_sphere(pr->p, d, p, u, dh);
     if (pr->xform == 0 && pr->kind == 1) return segment_box(pr->p, pr->p + 3, d, p, u, dh);
+    if (pr->xform == 0 && pr->kind == 2) return segment_capsule(pr->p, d, p, u, dh);
     return fabs(d) - dh;                 /* other shapes and placed ones: isotropic bound */
 }
 

@@ -55,6 +55,12 @@ MUTANTS = [
     ("elongate_clamp", "q[a] = q[a] - fmin(fmax(q[a], -X->a[a]), X->a[a]);", "q[a] = q[a] - fmin(q[a], X->a[a]);"),
     ("repeat_rounding", "double k = floor(q[a] / c + 0.5);", "double k = floor(q[a] / c);"),
     ("twist_stretch_bound", "L = X->op == 2 ? 0.5 * (m + sqrt(m * m + 4.0)) : 1.0 + m;", "L = sqrt(1.0 + m * m);"),
+    ("segment_capsule_margin", "double rr = d > 0.0 ? q[6] + dh : q[6] - dh;", "double rr = d > 0.0 ? q[6] : q[6] - dh;"),
+    ("segment_capsule_far_ball", "ray_ball(ox - bax, oy - bay, oz - baz, rr, u, &t0[1], &t1[1]);",
+     "ray_ball(ox + bax, oy + bay, oz + baz, rr, u, &t0[1], &t1[1]);"),
+    ("segment_cylinder_cross_axis", "double vx = u[0] - k * bax, vy = u[1] - k * bay, vz = u[2] - k * baz;",
+     "double vx = u[0], vy = u[1], vz = u[2];"),
+    ("segment_capsule_exit", "if (t0[k] <= t1[k]) t = fmax(t, t1[k]);", "if (t0[k] <= t1[k]) t = fmax(t, t0[k]);"),
 ]
 
 

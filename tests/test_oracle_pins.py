@@ -839,8 +839,25 @@ def _csg_scene():
                    stepping=W.SEGMENT)
 
 
+def _capsule_scene():
+    """A hard union of capsules in several orientations, and a capsule minus
+    a sphere: every capsule bounds moves by its ray bound."""
+    prims = (W.Prim(W.CAPSULE, (-0.6, 0.0, 0.0, 0.6, 0.0, 0.0, 0.15)),
+             W.Prim(W.CAPSULE, (0.0, -0.7, 0.3, 0.1, 0.7, 0.2, 0.1)),
+             W.Prim(W.CAPSULE, (-0.5, -0.5, -0.6, 0.5, 0.4, 0.6, 0.08)),
+             W.Prim(W.CAPSULE, (0.7, 0.7, -0.8, 0.7, 0.72, 0.8, 0.12)),
+             W.Prim(W.CAPSULE, (-0.8, 0.6, 0.6, -0.2, 0.6, 0.6, 0.2)),
+             W.Prim(W.SPHERE, (-0.5, 0.6, 0.6, 0.18)))
+    r0 = W.prim_program([0, 1, 2, 3])
+    r1 = (W.Node(W.PRIM, 4), W.Node(W.PRIM, 5), W.Node(W.SUBTRACT))
+    regs = (W.Region(r0, 1.0, 5.0, 0.5, 1.4), W.Region(r1, 0.5, 2.0, 0.0, 1.2))
+    return W.Scene(prims, regs, 1.0, (-1.2, -1.2, -1.2), (1.2, 1.2, 1.2), delta=1e-3,
+                   stepping=W.SEGMENT)
+
+
 SEGMENT_SCENES = {
     "csg": _csg_scene,
+    "capsules": _capsule_scene,
     "sphere": lambda: W.sphere_pencil().scene,
     "slab": lambda: W.three_layer_slab().scene,
     "glass": lambda: W.glass_container().scene,
@@ -917,6 +934,53 @@ def test_segment_step_exact_for_planes_and_spheres():
     # a ray that misses the grown sphere is bounded by the bounding box only
     t = O.segment_step(sph, (1.2, 0.0, 2.0), np.array([0.0, 0.0, -1.0]))
     assert math.isclose(t, 5.0 - d / 2, rel_tol=1e-12)
+
+
+def test_segment_step_exact_for_capsules():
+    # capsule from (-h, 0, 0) to (h, 0, 0), radius r: the move ends on the
+    # delta/2-offset surface of the cylinder or of an end ball
+    d, h, r = 1e-3, 0.5, 0.2
+    cap = W.Scene((W.Prim(W.CAPSULE, (-h, 0.0, 0.0, h, 0.0, 0.0, r)),),
+                  (W.Region(W.prim_program([0]), 0.0, 1.0, 0.0, 1.5),), 1.0,
+                  (-3, -3, -3), (3, 3, 3), delta=d, stepping=W.SEGMENT)
+    rg, rs = r + d / 2, r - d / 2
+    down, along = np.array([0.0, 0.0, -1.0]), np.array([-1.0, 0.0, 0.0])
+    for x0 in (-0.4, 0.0, 0.3):
+        # outside, across the axis: entry of the grown cylinder
+        assert math.isclose(O.segment_step(cap, (x0, 0.0, 2.0), down), 2.0 - rg, rel_tol=1e-12)
+        # inside, across the axis at offset y0: exit of the shrunk cylinder
+        for y0 in (0.0, 0.1, 0.19):
+            t = O.segment_step(cap, (x0, y0, 0.0), np.array([0.0, 0.0, 1.0]))
+            assert math.isclose(t, math.sqrt(rs * rs - y0 * y0), rel_tol=1e-12)
+    for y0 in (0.0, 0.1, 0.2):
+        # outside, parallel to the axis: entry of the grown end ball
+        t = O.segment_step(cap, (2.0, y0, 0.0), along)
+        assert math.isclose(t, 2.0 - h - math.sqrt(rg * rg - y0 * y0), rel_tol=1e-12)
+        # inside, along the axis: exit through the far end ball
+        t = O.segment_step(cap, (0.1, y0 * 0.5, 0.0), np.array([1.0, 0.0, 0.0]))
+        assert math.isclose(t, h - 0.1 + math.sqrt(rs * rs - (y0 * 0.5) ** 2), rel_tol=1e-12)
+    # a ray that misses the grown capsule is bounded by the bounding box only
+    t = O.segment_step(cap, (0.0, 0.3, 2.0), down)
+    assert math.isclose(t, 5.0 - d / 2, rel_tol=1e-12)
+    # oblique rays from outside, aimed near the capsule: no sampled point of
+    # the move comes closer than delta/2, and a ray that meets the capsule
+    # stops where the SDF is delta/2
+    rng = np.random.default_rng(3)
+    hit = 0
+    for _ in range(60):
+        p = rng.uniform(-1.5, 1.5, 3)
+        if O.region_sdf(cap, 0, p) <= d:
+            continue
+        aim = np.array([rng.uniform(-h - r, h + r), rng.normal(0.0, 0.12), rng.normal(0.0, 0.12)])
+        u = aim - p
+        u /= np.linalg.norm(u)
+        t = O.segment_step(cap, p, u)
+        ts = np.linspace(0.0, t, 400)
+        dist = np.array([O.region_sdf(cap, 0, p + s * u) for s in ts])
+        assert dist.min() >= d / 2 - 1e-12
+        if t < 4.0 and abs(O.region_sdf(cap, 0, p + t * u) - d / 2) < 1e-9:
+            hit += 1
+    assert hit > 10
 
 
 def _seg(sc):
