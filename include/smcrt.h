@@ -136,11 +136,14 @@ enum smcrt_stepping {
     SMCRT_STEP_SPHERE_TRACING = 0,
     /* Segment stepping (Sec. 5 names segment tracing for packets moving
      * nearly parallel to a surface): move max(d_min - delta/2, B), where B
-     * bounds the move along the packet's own direction -- for every box
-     * and sphere of a region built by hard CSG (union, intersection,
-     * subtraction), the distance along the ray to its surface offset by
-     * delta/2; for regions with a smooth union and for capsules |d| -
-     * delta/2; for the bounding box its exit distance less delta/2.  The
+     * bounds the move along the packet's own direction -- for every box,
+     * sphere and capsule of a region built by hard CSG (union,
+     * intersection, subtraction), the distance along the ray to its surface
+     * offset by delta/2; for regions with a smooth union, for tori,
+     * cylinders and placed primitives |d| - delta/2 (in mixed precision also
+     * for a union of 16 or more primitives, which is evaluated through a
+     * grid of per-cell candidate lists); for the bounding box
+     * its exit distance less delta/2.  The
      * move stops delta/2 short of the first surface it would reach, and the
      * interface handling is unchanged.  Same transport, fewer steps. */
     SMCRT_STEP_SEGMENT = 1

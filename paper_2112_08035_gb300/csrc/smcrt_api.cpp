@@ -468,7 +468,9 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     const size_t o_coff = take(sizeof(int32_t) * cg.off.size());
     const size_t o_clist = take(sizeof(int32_t) * cg.list.size());
     std::vector<int32_t> segp(sc->stepping == SMCRT_STEP_SEGMENT ? kMaxPrims : 0);
-    const int nseg = segp.empty() ? 0 : hard_region_prims(sc, segp.data());
+    // a culled region bounds segment moves by its (culled) distance, like a
+    // soft region: ray bounds over all its primitives would undo the culling
+    const int nseg = segp.empty() ? 0 : hard_region_prims(sc, segp.data(), cg.region);
     const size_t o_seg = take(sizeof(int32_t) * nseg);
     const size_t o_xf64 = take(sizeof(double) * xf64.size());
     const size_t o_xf32 = take(sizeof(float4) * xf32.size());

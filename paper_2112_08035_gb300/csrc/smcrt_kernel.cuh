@@ -484,7 +484,9 @@ __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float
     } else {   // regions in index order: before, the culled one, after
         const int2 rr = (*(S.rrange + S.cull_region));
         run_prog32<true, G>(S, 0, rr.x, x, y, z, sel, &E);
-        region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, S.cull_op == 2);
+        // the culled region's distance always bounds segment moves
+        // isotropically (its primitives are not in seg_prims)
+        region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, true);
         run_prog32<true, G>(S, rr.y, S.ninstr, x, y, z, sel, &E);
     }
     const float db = box32(x, y, z, S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2]);
@@ -639,8 +641,9 @@ __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, 
 // sphere and box of a hard-CSG region, the distance along the ray to its
 // surface offset by delta/2 (grown when p is outside, shrunk when inside),
 // over which the primitive's |SDF| stays above delta/2 and its sign cannot
-// change; |d| - delta/2 for soft regions (dsoft) and capsules; the exit of
-// the bounding box shrunk by delta/2.  The caller moves max(d_min - delta/2,
+// change; the same for capsules (cylinder and end balls); |d| - delta/2 for
+// soft regions (dsoft) and other shapes; the exit of the bounding box shrunk
+// by delta/2.  The caller moves max(d_min - delta/2,
 // bound).  FP64: the reference's operations in its order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double seg_sphere64(const double *P, double d, double px, double py, double pz,
@@ -689,6 +692,101 @@ __device__ __forceinline__ double seg_box64(double cx, double cy, double cz, dou
     return tf > 0.0 ? tf : 0.0;          // inside: exit of the shrunk box
 }
 
+// Ray interval [t0, t1] inside the ball of radius rr whose centre is at
+// p - o (t0 > t1: missed); the far root comes from the near one through the
+// product of the roots.
+__device__ __forceinline__ void ray_ball64(double ox, double oy, double oz, double rr, double ux, double uy,
+                                           double uz, double &t0, double &t1)
+{
+    const double b = ox * ux + oy * uy + oz * uz;
+    const double cc = ox * ox + oy * oy + oz * oz - rr * rr;
+    const double disc = b * b - cc;
+    t0 = __longlong_as_double(0x7ff0000000000000LL);
+    t1 = -t0;
+    if (disc < 0.0) return;
+    const double sq = sqrt(disc);
+    if (b > 0.0) {
+        const double q = -(b + sq);
+        t0 = q; t1 = cc / q;
+    } else {
+        const double q = sq - b;
+        if (q > 0.0) { t1 = q; t0 = cc / q; }
+        else { t0 = 0.0; t1 = 0.0; }
+    }
+}
+
+// Ray interval inside the cylinder of radius rr about the axis a + s ba
+// between the planes s = 0 and s = 1 (o = p - a, L2 = |ba|^2); the cross-axis
+// parts of o and u are formed first.
+__device__ __forceinline__ void ray_cylinder64(double ox, double oy, double oz, double bax, double bay,
+                                               double baz, double L2, double rr, double ux, double uy,
+                                               double uz, double &t0, double &t1)
+{
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const double uw = ux * bax + uy * bay + uz * baz;
+    const double ow = ox * bax + oy * bay + oz * baz;
+    double lo = -inf, hi = inf;
+    t0 = inf; t1 = -inf;
+    if (uw != 0.0) {                     // between the end planes
+        const double s0 = -ow / uw, s1 = (L2 - ow) / uw;
+        lo = fmin(s0, s1); hi = fmax(s0, s1);
+    } else if (ow < 0.0 || ow > L2) {
+        return;
+    }
+    const double k = uw / L2, m = ow / L2;
+    const double vx = ux - k * bax, vy = uy - k * bay, vz = uz - k * baz;
+    const double wx = ox - m * bax, wy = oy - m * bay, wz = oz - m * baz;
+    const double A = vx * vx + vy * vy + vz * vz;
+    const double B = wx * vx + wy * vy + wz * vz;
+    const double C = wx * wx + wy * wy + wz * wz - rr * rr;
+    if (A > 0.0) {                       // A t^2 + 2 B t + C <= 0
+        const double disc = B * B - A * C;
+        if (disc < 0.0) return;
+        const double sq = sqrt(disc);
+        double c0, c1;
+        if (B > 0.0) {
+            const double q = -(B + sq);
+            c0 = q / A; c1 = C / q;
+        } else {
+            const double q = sq - B;
+            if (q > 0.0) { c1 = q / A; c0 = C / q; }
+            else { c0 = 0.0; c1 = 0.0; }
+        }
+        lo = fmax(lo, c0); hi = fmin(hi, c1);
+    } else if (C > 0.0) {
+        return;
+    }
+    t0 = lo; t1 = hi;
+}
+
+// Capsule (convex: the cylinder between its end planes and the two end
+// balls): from outside the earliest entry of a part of the grown capsule,
+// from inside the latest exit from a part of the shrunk one.
+__device__ __forceinline__ double seg_capsule64(const double *P, double d, double px, double py, double pz,
+                                                double ux, double uy, double uz, double dh)
+{
+    const double rr = d > 0.0 ? __ldg(P + 6) + dh : __ldg(P + 6) - dh;
+    const double ox = px - __ldg(P), oy = py - __ldg(P + 1), oz = pz - __ldg(P + 2);
+    const double bax = __ldg(P + 3), bay = __ldg(P + 4), baz = __ldg(P + 5), L2 = __ldg(P + 7);
+    double a0, a1, b0, b1, c0, c1;
+    ray_ball64(ox, oy, oz, rr, ux, uy, uz, a0, a1);
+    ray_ball64(ox - bax, oy - bay, oz - baz, rr, ux, uy, uz, b0, b1);
+    ray_cylinder64(ox, oy, oz, bax, bay, baz, L2, rr, ux, uy, uz, c0, c1);
+    double t;
+    if (d > 0.0) {
+        t = __longlong_as_double(0x7ff0000000000000LL);
+        if (a0 <= a1 && a1 >= 0.0) t = fmin(t, a0);
+        if (b0 <= b1 && b1 >= 0.0) t = fmin(t, b0);
+        if (c0 <= c1 && c1 >= 0.0) t = fmin(t, c0);
+    } else {
+        t = 0.0;
+        if (a0 <= a1) t = fmax(t, a1);
+        if (b0 <= b1) t = fmax(t, b1);
+        if (c0 <= c1) t = fmax(t, c1);
+    }
+    return t > 0.0 ? t : 0.0;
+}
+
 template <bool G>
 static __device__ __noinline__ double segment_bound64(const DevScene &S, double dsoft, double dbox, double px,
                                                       double py, double pz, double ux, double uy, double uz)
@@ -708,8 +806,10 @@ static __device__ __noinline__ double segment_bound64(const DevScene &S, double 
             const double *P = S.p64 + 8 * i;
             b = seg_box64(__ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5), d, px,
                           py, pz, ux, uy, uz, dh);
+        } else if (kind == 2) {
+            b = seg_capsule64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, dh);
         } else {
-            b = fabs(d) - dh;            // capsule: isotropic
+            b = fabs(d) - dh;            // other shapes and placed ones: isotropic
         }
         t = fmin(t, b);
     }
@@ -764,6 +864,93 @@ __device__ __forceinline__ float seg_box32(float cx, float cy, float cz, float h
     return tf > 0.f ? tf : 0.f;
 }
 
+__device__ __forceinline__ void ray_ball32(float ox, float oy, float oz, float rr, float ux, float uy, float uz,
+                                           float &t0, float &t1)
+{
+    const float b = ox * ux + oy * uy + oz * uz;
+    const float cc = ox * ox + oy * oy + oz * oz - rr * rr;
+    const float disc = b * b - cc;
+    t0 = __int_as_float(0x7f800000);
+    t1 = -t0;
+    if (disc < 0.f) return;
+    const float sq = sqrtf(disc);
+    if (b > 0.f) {
+        const float q = -(b + sq);
+        t0 = q; t1 = cc / q;
+    } else {
+        const float q = sq - b;
+        if (q > 0.f) { t1 = q; t0 = cc / q; }
+        else { t0 = 0.f; t1 = 0.f; }
+    }
+}
+
+__device__ __forceinline__ void ray_cylinder32(float ox, float oy, float oz, float bax, float bay, float baz,
+                                               float iL2, float rr, float ux, float uy, float uz, float &t0,
+                                               float &t1)
+{
+    const float inf = __int_as_float(0x7f800000);
+    const float L2 = bax * bax + bay * bay + baz * baz;
+    const float uw = ux * bax + uy * bay + uz * baz;
+    const float ow = ox * bax + oy * bay + oz * baz;
+    float lo = -inf, hi = inf;
+    t0 = inf; t1 = -inf;
+    if (uw != 0.f) {
+        const float s0 = -ow / uw, s1 = (L2 - ow) / uw;
+        lo = fminf(s0, s1); hi = fmaxf(s0, s1);
+    } else if (ow < 0.f || ow > L2) {
+        return;
+    }
+    const float k = uw * iL2, m = ow * iL2;
+    const float vx = ux - k * bax, vy = uy - k * bay, vz = uz - k * baz;
+    const float wx = ox - m * bax, wy = oy - m * bay, wz = oz - m * baz;
+    const float A = vx * vx + vy * vy + vz * vz;
+    const float B = wx * vx + wy * vy + wz * vz;
+    const float C = wx * wx + wy * wy + wz * wz - rr * rr;
+    if (A > 0.f) {
+        const float disc = B * B - A * C;
+        if (disc < 0.f) return;
+        const float sq = sqrtf(disc);
+        float c0, c1;
+        if (B > 0.f) {
+            const float q = -(B + sq);
+            c0 = q / A; c1 = C / q;
+        } else {
+            const float q = sq - B;
+            if (q > 0.f) { c1 = q / A; c0 = C / q; }
+            else { c0 = 0.f; c1 = 0.f; }
+        }
+        lo = fmaxf(lo, c0); hi = fminf(hi, c1);
+    } else if (C > 0.f) {
+        return;
+    }
+    t0 = lo; t1 = hi;
+}
+
+// FP32 capsule bound; the tables hold (a, r) and (b - a, 1 / |b - a|^2).
+__device__ __forceinline__ float seg_capsule32(float4 A, float4 Bv, float d, float px, float py, float pz,
+                                               float ux, float uy, float uz, float dh)
+{
+    const float rr = d > 0.f ? A.w + dh : A.w - dh;
+    const float ox = px - A.x, oy = py - A.y, oz = pz - A.z;
+    float a0, a1, b0, b1, c0, c1;
+    ray_ball32(ox, oy, oz, rr, ux, uy, uz, a0, a1);
+    ray_ball32(ox - Bv.x, oy - Bv.y, oz - Bv.z, rr, ux, uy, uz, b0, b1);
+    ray_cylinder32(ox, oy, oz, Bv.x, Bv.y, Bv.z, Bv.w, rr, ux, uy, uz, c0, c1);
+    float t;
+    if (d > 0.f) {
+        t = __int_as_float(0x7f800000);
+        if (a0 <= a1 && a1 >= 0.f) t = fminf(t, a0);
+        if (b0 <= b1 && b1 >= 0.f) t = fminf(t, b0);
+        if (c0 <= c1 && c1 >= 0.f) t = fminf(t, c0);
+    } else {
+        t = 0.f;
+        if (a0 <= a1) t = fmaxf(t, a1);
+        if (b0 <= b1) t = fmaxf(t, b1);
+        if (c0 <= c1) t = fmaxf(t, c1);
+    }
+    return t > 0.f ? t : 0.f;
+}
+
 template <bool G>
 static __device__ __noinline__ float segment_bound32(const DevScene &S, float dsoft, float dbox, float px,
                                                      float py, float pz, float ux, float uy, float uz)
@@ -783,6 +970,8 @@ static __device__ __noinline__ float segment_bound32(const DevScene &S, float ds
         } else if (kind == 1) {
             const float4 A = (*(S.p32 + 2 * i)), B = (*(S.p32 + 2 * i + 1));
             b = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, px, py, pz, ux, uy, uz, iux, iuy, iuz, dh);
+        } else if (kind == 2) {
+            b = seg_capsule32((*(S.p32 + 2 * i)), (*(S.p32 + 2 * i + 1)), d, px, py, pz, ux, uy, uz, dh);
         } else {
             b = fabsf(d) - dh;
         }

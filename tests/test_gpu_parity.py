@@ -64,6 +64,7 @@ SMALL = [
     (W.sphere_pencil, 3000),
     (W.three_layer_slab, 1500),
     (W.vessel_network, 300),
+    (W.vessel_network_hard, 300),
     (W.glass_container, 600),
 ]
 
@@ -145,6 +146,7 @@ MIXED = [
     (W.sphere_pencil, 200_000, 20_000),
     (W.three_layer_slab, 200_000, 10_000),
     (W.vessel_network, 40_000, 2_000),
+    (W.vessel_network_hard, 40_000, 2_000),
     (W.glass_container, 100_000, 5_000),
 ]
 

@@ -862,6 +862,7 @@ SEGMENT_SCENES = {
     "slab": lambda: W.three_layer_slab().scene,
     "glass": lambda: W.glass_container().scene,
     "vessel": lambda: W.vessel_network().scene,
+    "vessel_hard": lambda: W.vessel_network_hard().scene,
     "gallery": lambda: W.sdf_gallery().scene,
 }
 

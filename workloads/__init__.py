@@ -241,23 +241,33 @@ def vessel_tree_capsules(seed: int = 3, n: int = 64, cube: float = 0.5):
 
 
 def vessel_network(npackets: int = 100_000_000, seed: int = 3, precision: str = "mixed",
-                   grid_n: int = 200, ncap: int = 64) -> Workload:
+                   grid_n: int = 200, ncap: int = 64, smooth: bool = True) -> Workload:
     """5 mm tissue cube (mu_a=0.5, mu_s=100, g=0.9, n=1.4) with a 64-capsule
     smooth-union (k = 10 um) vessel tree (blood mu_a=20, mu_s=200, g=0.98,
-    n=1.4); uniform square illumination of the top face; 200^3 grid."""
+    n=1.4); uniform square illumination of the top face; 200^3 grid.
+    smooth=False joins the capsules by a plain union instead."""
     caps = vessel_tree_capsules(seed, ncap)
     prims = [Prim(BOX, (0.25, 0.25, 0.25, 0.25, 0.25, 0.25))]
     for a, b, r in caps:
         prims.append(Prim(CAPSULE, a + b + (r,)))
     regions = (
         Region(prim_program([0]), 0.5, 100.0, 0.90, 1.4),
-        Region(prim_program(list(range(1, ncap + 1)), SMOOTH_UNION, 1e-3), 20.0, 200.0, 0.98, 1.4),
+        Region(prim_program(list(range(1, ncap + 1)), SMOOTH_UNION, 1e-3) if smooth
+               else prim_program(list(range(1, ncap + 1))), 20.0, 200.0, 0.98, 1.4),
     )
     scene = Scene(tuple(prims), regions, 1.0, (-0.03, -0.03, -0.03), (0.53, 0.53, 0.53))
-    return Workload(f"vessel_network_{ncap}cap_{grid_n}c", scene,
+    return Workload(f"vessel_network_{ncap}cap_{grid_n}c" + ("" if smooth else "_hard"), scene,
                     Source(SQUARE, (0.25, 0.25, 0.525), (0.0, 0.0, -1.0), 0.25),
                     Grid((0.0, 0.0, 0.0), (0.5, 0.5, 0.5), (grid_n, grid_n, grid_n)),
                     npackets, seed, precision)
+
+
+def vessel_network_hard(npackets: int = 2_000_000, seed: int = 3, precision: str = "mixed",
+                        grid_n: int = 100) -> Workload:
+    """The vessel tree with a plain union of its 64 capsules (sharp joints):
+    a hard region of capsules, so segment stepping bounds moves by ray-capsule
+    distances (and, in mixed mode, by the culled region's distance)."""
+    return vessel_network(npackets, seed, precision, grid_n, 64, smooth=False)
 
 
 def glass_container(npackets: int = 100_000_000, seed: int = 5, precision: str = "mixed",
