@@ -761,8 +761,10 @@ __device__ __forceinline__ void ray_cylinder64(double ox, double oy, double oz, 
 
 // Capsule (convex: the cylinder between its end planes and the two end
 // balls): from outside the earliest entry of a part of the grown capsule,
-// from inside the latest exit from a part of the shrunk one.
-__device__ __forceinline__ double seg_capsule64(const double *P, double d, double px, double py, double pz,
+// from inside the latest exit from a part of the shrunk one.  Out of line in
+// both precisions: inlined into the bound routine, its three quadratics cost
+// scenes without capsules 7 % (the routine's registers and size).
+static __device__ __noinline__ double seg_capsule64(const double *P, double d, double px, double py, double pz,
                                                 double ux, double uy, double uz, double dh)
 {
     const double rr = d > 0.0 ? __ldg(P + 6) + dh : __ldg(P + 6) - dh;
@@ -927,7 +929,7 @@ __device__ __forceinline__ void ray_cylinder32(float ox, float oy, float oz, flo
 }
 
 // FP32 capsule bound; the tables hold (a, r) and (b - a, 1 / |b - a|^2).
-__device__ __forceinline__ float seg_capsule32(float4 A, float4 Bv, float d, float px, float py, float pz,
+static __device__ __noinline__ float seg_capsule32(float4 A, float4 Bv, float d, float px, float py, float pz,
                                                float ux, float uy, float uz, float dh)
 {
     const float rr = d > 0.f ? A.w + dh : A.w - dh;
