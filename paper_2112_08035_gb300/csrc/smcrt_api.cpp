@@ -241,6 +241,7 @@ struct smcrt_ctx {
     std::thread sched;
     bool stop = false;
     bool sched_started = false;
+    int sched_error = 0;   // the scheduler could not set up: every job fails with this
     int64_t launches = 0;
     int64_t running = 0;
     size_t mem_in_use = 0;
@@ -755,21 +756,30 @@ int alloc_defer(Job &j, cudaStream_t st)
 // next round after admission; completion is read from the totals snapshot.
 void scheduler(smcrt_ctx *ctx)
 {
-    cudaSetDevice(ctx->device);
-    cudaStream_t st, st2;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
-    cudaEvent_t ev_fork, ev_join;
-    cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+    // Setup: every call is checked; on a failure the scheduler fails all jobs
+    // with the error instead of running rounds on missing buffers.
+    // SMCRT_FAULT_SCHEDULER_SETUP (any value) makes the first allocation
+    // report failure: host-side injection for the error-path tests.
+    int setup_rc = SMCRT_OK;
+    const bool inject = std::getenv("SMCRT_FAULT_SCHEDULER_SETUP") != nullptr;
+    auto chk = [&](cudaError_t e, int rc) {
+        if (e != cudaSuccess && setup_rc == SMCRT_OK) setup_rc = rc;
+    };
+    chk(cudaSetDevice(ctx->device), SMCRT_ERR_CUDA);
+    cudaStream_t st = nullptr, st2 = nullptr;
+    chk(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), SMCRT_ERR_CUDA);
+    chk(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking), SMCRT_ERR_CUDA);
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    chk(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming), SMCRT_ERR_CUDA);
+    chk(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming), SMCRT_ERR_CUDA);
     int *d_status = nullptr;
     smcrt_totals *d_tot = nullptr;
-    cudaMalloc(&d_status, sizeof(int));
-    cudaMemset(d_status, 0, sizeof(int));
-    cudaMalloc(&d_tot, sizeof(smcrt_totals) * kMaxSlots);
-    cudaMemset(d_tot, 0, sizeof(smcrt_totals) * kMaxSlots);
+    chk(inject ? cudaErrorMemoryAllocation : cudaMalloc(&d_status, sizeof(int)), SMCRT_ERR_NO_MEMORY);
+    if (d_status) chk(cudaMemset(d_status, 0, sizeof(int)), SMCRT_ERR_CUDA);
+    chk(cudaMalloc(&d_tot, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_NO_MEMORY);
+    if (d_tot) chk(cudaMemset(d_tot, 0, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_CUDA);
     int *h_status = nullptr;
-    cudaMallocHost(&h_status, sizeof(int));
+    chk(cudaMallocHost(&h_status, sizeof(int)), SMCRT_ERR_NO_MEMORY);
     const int threads = 128;
     const int occ_m = std::max(1, occupancy_mixed(threads, default_variant(SMCRT_MIXED))),
               occ_d = std::max(1, occupancy_fp64(threads, default_variant(SMCRT_FP64)));
@@ -794,11 +804,13 @@ void scheduler(smcrt_ctx *ctx)
     } buf[kRoundsInFlight];
     const bool trace = std::getenv("SMCRT_TRACE") != nullptr;
     for (auto &b : buf) {
-        cudaMallocHost(&b.h_tab, sizeof(JobWork) * 2 * kMaxSlots);
-        cudaMalloc(&b.d_tab, sizeof(JobWork) * 2 * kMaxSlots);
-        cudaMallocHost(&b.h_tot, sizeof(smcrt_totals) * kMaxSlots);
-        cudaEventCreate(&b.ev);
-        cudaEventCreate(&b.ev0);
+        if (setup_rc != SMCRT_OK) break;
+        chk(cudaMallocHost(&b.h_tab, sizeof(JobWork) * 2 * kMaxSlots), SMCRT_ERR_NO_MEMORY);
+        chk(cudaMalloc(&b.d_tab, sizeof(JobWork) * 2 * kMaxSlots), SMCRT_ERR_NO_MEMORY);
+        chk(cudaMallocHost(&b.h_tot, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_NO_MEMORY);
+        chk(cudaEventCreate(&b.ev), SMCRT_ERR_CUDA);
+        chk(cudaEventCreate(&b.ev0), SMCRT_ERR_CUDA);
+        if (setup_rc != SMCRT_OK) break;
         std::memset(b.h_tab, 0, sizeof(JobWork) * 2 * kMaxSlots);
         for (int gen = 0; gen < 2; ++gen) {
             const int off = gen ? kNumVariants : 0;
@@ -814,9 +826,28 @@ void scheduler(smcrt_ctx *ctx)
             cudaEventRecord(ev_join, st2);
             cudaStreamWaitEvent(st, ev_join, 0);
             cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
-            cudaStreamEndCapture(st, &g);
-            cudaGraphInstantiate(gen ? &b.graph_g : &b.graph, g, 0);
+            chk(cudaStreamEndCapture(st, &g), SMCRT_ERR_CUDA);
+            if (setup_rc != SMCRT_OK) break;
+            chk(cudaGraphInstantiate(gen ? &b.graph_g : &b.graph, g, 0), SMCRT_ERR_CUDA);
             cudaGraphDestroy(g);
+        }
+    }
+    if (setup_rc != SMCRT_OK) {
+        // fail every queued job, and every later one, until the context ends
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        ctx->sched_error = setup_rc;
+        for (;;) {
+            while (!ctx->queue.empty()) {
+                auto j = ctx->queue.front();
+                ctx->queue.pop_front();
+                j->status = setup_rc;
+                j->done = true;
+                j->t_done = now_s();
+            }
+            ctx->to_release.clear();
+            ctx->cv_done.notify_all();
+            if (ctx->stop) break;
+            ctx->cv_work.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
         }
     }
 
@@ -841,7 +872,7 @@ void scheduler(smcrt_ctx *ctx)
         ctx->cv_done.notify_all();
     };
 
-    for (;;) {
+    for (; setup_rc == SMCRT_OK;) {
         // ---- admission (FIFO, by slots and device memory) and releases
         std::vector<std::shared_ptr<Job>> newly, released;
         {
@@ -1002,7 +1033,7 @@ void scheduler(smcrt_ctx *ctx)
         cur = 1 - cur;
     }
     // shut down: wait for rounds, free everything still held
-    cudaStreamSynchronize(st);
+    if (st) cudaStreamSynchronize(st);
     for (auto &j : active) free_job_device(*j, st);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1010,23 +1041,23 @@ void scheduler(smcrt_ctx *ctx)
         ctx->to_release.clear();
         for (auto &kv : ctx->jobs) free_job_device(*kv.second, st);   // done but never waited
     }
-    cudaStreamSynchronize(st);
+    if (st) cudaStreamSynchronize(st);
     for (auto &b : buf) {
-        cudaGraphExecDestroy(b.graph);
-        cudaGraphExecDestroy(b.graph_g);
-        cudaEventDestroy(b.ev);
-        cudaEventDestroy(b.ev0);
-        cudaFreeHost(b.h_tab);
-        cudaFreeHost(b.h_tot);
-        cudaFree(b.d_tab);
+        if (b.graph) cudaGraphExecDestroy(b.graph);
+        if (b.graph_g) cudaGraphExecDestroy(b.graph_g);
+        if (b.ev) cudaEventDestroy(b.ev);
+        if (b.ev0) cudaEventDestroy(b.ev0);
+        if (b.h_tab) cudaFreeHost(b.h_tab);
+        if (b.h_tot) cudaFreeHost(b.h_tot);
+        if (b.d_tab) cudaFree(b.d_tab);
     }
-    cudaFreeHost(h_status);
-    cudaEventDestroy(ev_fork);
-    cudaEventDestroy(ev_join);
-    cudaFree(d_tot);
-    cudaFree(d_status);
-    cudaStreamDestroy(st2);
-    cudaStreamDestroy(st);
+    if (h_status) cudaFreeHost(h_status);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (d_tot) cudaFree(d_tot);
+    if (d_status) cudaFree(d_status);
+    if (st2) cudaStreamDestroy(st2);
+    if (st) cudaStreamDestroy(st);
 }
 
 void start_scheduler(smcrt_ctx *ctx)
@@ -1319,6 +1350,7 @@ int smcrt_submit(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *s
     j->bytes = job_bytes(*grid);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->sched_error) return ctx->sched_error;
         if (j->bytes > ctx->budget) return SMCRT_ERR_NO_MEMORY;
         j->id = ctx->next_job_id++;
         ctx->jobs[j->id] = j;

@@ -92,3 +92,43 @@ def test_timeout_keeps_job(ctx):
     if timed_out:
         f, t, _ = ctx.wait(jid, 300.0)
         assert t["packets"] == big.npackets
+
+
+_SETUP_FAILURE_CHILD = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import paper_2112_08035_gb300 as smc
+import workloads as W
+ctx = smc.Context(0)
+jid = ctx.submit(W.sphere_pencil(1000, 1, "mixed"))
+try:
+    ctx.wait(jid, 60.0)
+    print("waited: no error")
+except smc.SmcrtError as e:
+    print("wait error", e.code)
+try:
+    ctx.submit(W.sphere_pencil(1000, 2, "mixed"))
+    print("submitted: no error")
+except smc.SmcrtError as e:
+    print("submit error", e.code)
+ctx.close()
+print("closed")
+"""
+
+
+def test_scheduler_setup_failure_fails_jobs_cleanly():
+    # a host-side injected allocation failure in the scheduler's setup: the
+    # queued job completes with the error, later submissions return it at
+    # once, and the context closes (no GPU fault is involved)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SMCRT_FAULT_SCHEDULER_SETUP="1")
+    r = subprocess.run([sys.executable, "-c", _SETUP_FAILURE_CHILD, root], env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.split("\n")
+    assert f"wait error {smc.ERR_NO_MEMORY}" in lines, r.stdout
+    assert f"submit error {smc.ERR_NO_MEMORY}" in lines, r.stdout
+    assert "closed" in lines, r.stdout
