@@ -162,18 +162,38 @@ class ClockSampler:
 
 def oracle_sample(wl, seconds: float, id_base: int = 0):
     """Time the FP64 oracle, as it stands, on a bounded sample sized to take
-    about ``seconds``; returns (packets/s, packets, threads, totals)."""
+    about ``seconds``, run as two halves of consecutive ids; returns
+    (packets/s, packets, threads, per-packet records, the halves' fluence
+    maps)."""
+    import numpy as np
     import oracle as O
     threads = os.cpu_count() or 1
     n0 = 2000
     t0 = time.perf_counter()
     O.run(wl.with_packets(n0), id_base, id_base + n0, threads=threads, fluence=True)
     rate0 = n0 / (time.perf_counter() - t0)
-    n = int(max(n0, min(5_000_000, rate0 * seconds)))
+    h = int(max(n0, min(5_000_000, rate0 * seconds))) // 2
     t0 = time.perf_counter()
-    _, tot, rec = O.run(wl.with_packets(n), id_base, id_base + n, threads=threads, records=True)
+    f1, _, r1 = O.run(wl.with_packets(h), id_base, id_base + h, threads=threads, records=True)
+    f2, _, r2 = O.run(wl.with_packets(h), id_base + h, id_base + 2 * h, threads=threads, records=True)
     dt = time.perf_counter() - t0
-    return n / dt, n, threads, tot, rec
+    return 2 * h / dt, 2 * h, threads, np.concatenate([r1, r2]), (f1, f2)
+
+
+def fluence_l2(gpu_flu, n_gpu: int, halves, n_half: int) -> dict:
+    """Relative L2 difference of the per-packet fluence maps (GPU against the
+    oracle sample), beside the oracle sample's own noise: the value a
+    consistent result shows, since the GPU's 1e7 packets add little noise.
+    The sample's noise is half the difference of its two half-sample maps."""
+    import numpy as np
+    f1 = halves[0].astype(np.float64) / n_half
+    f2 = halves[1].astype(np.float64) / n_half
+    po = 0.5 * (f1 + f2)
+    pg = gpu_flu.astype(np.float64) / n_gpu
+    norm = float(np.linalg.norm(po))
+    l2 = float(np.linalg.norm(pg - po)) / norm
+    noise = float(np.linalg.norm(f1 - f2)) / 2.0 / norm
+    return {"fluence_rel_l2": l2, "fluence_oracle_noise_rel_l2": noise, "fluence_l2_over_noise": l2 / noise}
 
 
 def reference_arm(args):
@@ -391,6 +411,7 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_sum = float(tt.item())
     totals_mixed = smc.totals_from_tensor(tot)
+    flu_legs = {"mixed": flu.cpu().numpy()}   # the last timed step's map (1e7 packets)
     value = args.packets * args.steps * world / t_sum
     kernel_s = t_sum / args.steps   # per-step device time ~ the packet kernel (one launch)
 
@@ -471,14 +492,15 @@ def main():
             evs.append((a, b))
         torch.cuda.synchronize()
         p.close()
-        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / nsteps, smc.totals_from_tensor(tot)
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / nsteps, smc.totals_from_tensor(tot), flu.cpu().numpy()
 
     if not args.quick:
         # ---- mixed precision with plain sphere tracing (the paper's step) ---
         totals_st = None
         if args.stepping != W.SPHERE_TRACING and args.precision == "mixed":
             log(f"mixed {value:.3e} packets/s; timing mixed with sphere tracing")
-            t_st, totals_st = timed_leg(wl_plain, "mixed", 3, min(args.packets, 2_000_000))
+            t_st, totals_st, flu_legs["mixed_sphere_tracing"] = timed_leg(wl_plain, "mixed", 3,
+                                                                          min(args.packets, 2_000_000))
             out["mixed_sphere_tracing"] = {"value": args.packets / t_st, "unit": UNIT, "ms_per_step": 1e3 * t_st,
                                            "segment_speedup": t_st / kernel_s}
         # ---- plain FP64 mode (sphere tracing) on the same workload ----------
@@ -498,6 +520,7 @@ def main():
         torch.cuda.synchronize()
         t64 = sum(a.elapsed_time(b) for a, b in e64) / 1e3 / args.fp64_steps
         totals_fp64 = smc.totals_from_tensor(tot)
+        flu_legs["fp64"] = flu.cpu().numpy()
         plan64.close()
         out["fp64"] = {"value": args.packets / t64, "unit": UNIT, "ms_per_step": 1e3 * t64,
                        "stepping": W.SPHERE_TRACING,
@@ -523,7 +546,7 @@ def main():
 
         log("oracle leg")
         # ---- accuracy against the FP64 oracle, and the oracle's CPU timing ----
-        o_pps, o_n, o_threads, o_tot, o_rec = oracle_sample(wl, args.oracle_seconds, id_base=0)
+        o_pps, o_n, o_threads, o_rec, o_halves = oracle_sample(wl, args.oracle_seconds, id_base=0)
         out["cpu_baseline"] = {"value": o_pps, "unit": UNIT, "cores": o_threads, "kind": "oracle",
                                "sample": f"{o_n} packets (ids 0..{o_n - 1}) of the same three_layer_slab "
                                          f"workload ({args.stepping} stepping), FP64, {o_threads} threads"}
@@ -540,10 +563,13 @@ def main():
                 d[k] = gv
                 d[f"{k}_oracle"] = float(ov.mean())
                 d[f"{k}_z"] = (gv - float(ov.mean())) / sig
+            d.update(fluence_l2(flu_legs[name], args.packets, o_halves, o_n // 2))
             acc[name] = d
         out["accuracy_vs_oracle"] = acc
         out["accuracy_vs_oracle"]["note"] = ("GPU at 1e7 packets vs oracle sample; z = difference / combined "
-                                             "MC sigma. FP64 mode is bit-identical to the oracle packet by packet")
+                                             "MC sigma; fluence_rel_l2 = |phi_gpu - phi_oracle| / |phi_oracle| "
+                                             "per packet, beside the oracle sample's own noise. FP64 mode is "
+                                             "bit-identical to the oracle packet by packet")
 
         if not args.no_paper_cases and args.precision == "mixed":
             log("paper cases (Table 2 sizes)")
