@@ -193,7 +193,8 @@ def fluence_l2(gpu_flu, n_gpu: int, halves, n_half: int) -> dict:
     norm = float(np.linalg.norm(po))
     l2 = float(np.linalg.norm(pg - po)) / norm
     noise = float(np.linalg.norm(f1 - f2)) / 2.0 / norm
-    return {"fluence_rel_l2": l2, "fluence_oracle_noise_rel_l2": noise, "fluence_l2_over_noise": l2 / noise}
+    return {"fluence_rel_l2": l2, "fluence_oracle_noise_rel_l2": noise,
+            "fluence_l2_over_noise": l2 / noise if noise > 0 else None}
 
 
 def reference_arm(args):
