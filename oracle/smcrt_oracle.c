@@ -782,6 +782,30 @@ static double segment_capsule(const double *q, double d, const double p[3], cons
     return t > 0.0 ? t : 0.0;
 }
 
+/* A sphere, box or capsule placed by a frame without a domain operation:
+ * the frame (rotation R, translation t, uniform scale s) maps the ray
+ * p + t' u to the local ray q + (t' / s) w with q = R^T (p - t) / s and the
+ * unit direction w = R^T u, and local distances are world distances over s.
+ * So the world bound is s times the local bound with margin dh / s; only the
+ * sign of d is used. */
+static double segment_xprim(const or_prim *pr, const or_xform *X, double d, const double p[3], const double u[3],
+                            double dh)
+{
+    double vx = p[0] - X->t[0], vy = p[1] - X->t[1], vz = p[2] - X->t[2];
+    double q[3], w[3];
+    q[0] = (X->rot[0] * vx + X->rot[3] * vy + X->rot[6] * vz) / X->s;
+    q[1] = (X->rot[1] * vx + X->rot[4] * vy + X->rot[7] * vz) / X->s;
+    q[2] = (X->rot[2] * vx + X->rot[5] * vy + X->rot[8] * vz) / X->s;
+    w[0] = X->rot[0] * u[0] + X->rot[3] * u[1] + X->rot[6] * u[2];
+    w[1] = X->rot[1] * u[0] + X->rot[4] * u[1] + X->rot[7] * u[2];
+    w[2] = X->rot[2] * u[0] + X->rot[5] * u[1] + X->rot[8] * u[2];
+    double hl = dh / X->s, t;
+    if (pr->kind == 0) t = segment_sphere(pr->p, d, q, w, hl);
+    else if (pr->kind == 1) t = segment_box(pr->p, pr->p + 3, d, q, w, hl);
+    else t = segment_capsule(pr->p, d, q, w, hl);
+    return X->s * t;
+}
+
 static double segment_prim(const or_scene *S, const or_prim *pr, const double p[3], const double u[3],
                            double dh)
 {
@@ -790,7 +814,9 @@ static double segment_prim(const or_scene *S, const or_prim *pr, const double p[
     if (pr->xform == 0 && pr->kind == 0) return segment_sphere(pr->p, d, p, u, dh);
     if (pr->xform == 0 && pr->kind == 1) return segment_box(pr->p, pr->p + 3, d, p, u, dh);
     if (pr->xform == 0 && pr->kind == 2) return segment_capsule(pr->p, d, p, u, dh);
-    return fabs(d) - dh;                 /* other shapes and placed ones: isotropic bound */
+    if (pr->xform > 0 && pr->kind <= 2 && S->xforms[pr->xform - 1].op == 0)
+        return segment_xprim(pr, &S->xforms[pr->xform - 1], d, p, u, dh);
+    return fabs(d) - dh;                 /* other shapes, domain operations: isotropic bound */
 }
 
 /* Largest safe move from p along u (scene evaluated at p in E). */

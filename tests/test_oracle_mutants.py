@@ -61,6 +61,10 @@ MUTANTS = [
     ("segment_cylinder_cross_axis", "double vx = u[0] - k * bax, vy = u[1] - k * bay, vz = u[2] - k * baz;",
      "double vx = u[0], vy = u[1], vz = u[2];"),
     ("segment_capsule_exit", "if (t0[k] <= t1[k]) t = fmax(t, t1[k]);", "if (t0[k] <= t1[k]) t = fmax(t, t0[k]);"),
+    ("segment_xprim_margin", "double hl = dh / X->s, t;", "double hl = dh, t;"),
+    ("segment_xprim_scale", "    return X->s * t;\n", "    return t;\n"),
+    ("segment_xprim_direction", "w[0] = X->rot[0] * u[0] + X->rot[3] * u[1] + X->rot[6] * u[2];",
+     "w[0] = X->rot[0] * u[0] + X->rot[1] * u[1] + X->rot[2] * u[2];"),
 ]
 
 

@@ -984,6 +984,44 @@ def test_segment_step_exact_for_capsules():
     assert hit > 10
 
 
+def test_segment_step_exact_for_placed_primitives():
+    # a frame without a domain operation maps rays to rays: the move ends on
+    # the world surface offset by delta/2 for any rotation and scale
+    d = 1e-3
+    down = np.array([0.0, 0.0, -1.0])
+
+    def one(prim):
+        return W.Scene((prim,), (W.Region(W.prim_program([0]), 0.0, 1.0, 0.0, 1.5),), 1.0,
+                       (-5, -5, -5), (5, 5, 5), delta=d, stepping=W.SEGMENT)
+    for s in (0.5, 1.0, 1.5):
+        rz = W.rotation((0, 0, 1), 90.0)
+        box = one(W.Prim(W.BOX, (0.0, 0.0, 0.0, 0.4, 0.3, 0.2), W.Xform(rot=rz, t=(0.2, 0.1, -1.0), s=s)))
+        assert math.isclose(O.segment_step(box, (0.2, 0.1, 1.0), down), 2.0 - (0.2 * s + d / 2), rel_tol=1e-12)
+        # along x the box shows its local y half extent (quarter turn about z)
+        t = O.segment_step(box, (3.0, 0.1, -1.0), np.array([-1.0, 0.0, 0.0]))
+        assert math.isclose(t, 3.0 - 0.2 - (0.3 * s + d / 2), rel_tol=1e-12)
+        # from inside along +y: the exit of the shrunk box at local x half extent
+        t = O.segment_step(box, (0.2, 0.1, -1.0), np.array([0.0, 1.0, 0.0]))
+        assert math.isclose(t, 0.4 * s - d / 2, rel_tol=1e-12)
+        sph = one(W.Prim(W.SPHERE, (0.0, 0.0, 0.0, 0.3), W.Xform(t=(0.0, 0.0, -1.0), s=s)))
+        for b in (0.0, 0.1):
+            rr = 0.3 * s + d / 2
+            t = O.segment_step(sph, (b, 0.0, 1.0), down)
+            assert math.isclose(t, 2.0 - math.sqrt(rr * rr - b * b), rel_tol=1e-12)
+        # a capsule along local x turned to lie along world y
+        cap = one(W.Prim(W.CAPSULE, (-0.5, 0.0, 0.0, 0.5, 0.0, 0.0, 0.1), W.Xform(rot=rz, t=(0.0, 0.0, -1.0), s=s)))
+        t = O.segment_step(cap, (0.0, 0.4 * s, 1.0), down)
+        assert math.isclose(t, 2.0 - (0.1 * s + d / 2), rel_tol=1e-12)
+        t = O.segment_step(cap, (0.0, 3.0, -1.0), np.array([0.0, -1.0, 0.0]))
+        assert math.isclose(t, 3.0 - 0.5 * s - (0.1 * s + d / 2), rel_tol=1e-12)
+    # a domain operation keeps the isotropic bound: the move is the
+    # sphere-tracing step d_min - delta/2
+    el = one(W.Prim(W.SPHERE, (0.0, 0.0, 0.0, 0.1), W.Xform(t=(0.0, 0.0, -1.0), op=W.ELONGATE, a=(0.3, 0.0, 0.0, 0.0))))
+    p = (0.0, 0.0, 1.0)
+    e = O.scene_eval(el, p)
+    assert math.isclose(O.segment_step(el, p, down), e["dmin"] - d / 2, rel_tol=1e-12)
+
+
 def _seg(sc):
     from dataclasses import replace
     return replace(sc, stepping=W.SEGMENT)
