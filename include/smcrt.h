@@ -138,9 +138,10 @@ enum smcrt_stepping {
      * nearly parallel to a surface): move max(d_min - delta/2, B), where B
      * bounds the move along the packet's own direction -- for every box,
      * sphere and capsule of a region built by hard CSG (union,
-     * intersection, subtraction), the distance along the ray to its surface
-     * offset by delta/2; for regions with a smooth union, for tori,
-     * cylinders and placed primitives |d| - delta/2 (in mixed precision also
+     * intersection, subtraction), also when placed by a frame without a
+     * domain operation, the distance along the ray to its surface offset by
+     * delta/2; for regions with a smooth union, for tori, cylinders and
+     * domain operations |d| - delta/2 (in mixed precision also
      * for a union of 16 or more primitives, which is evaluated through a
      * grid of per-cell candidate lists); for the bounding box
      * its exit distance less delta/2.  The

@@ -641,7 +641,8 @@ __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, 
 // sphere and box of a hard-CSG region, the distance along the ray to its
 // surface offset by delta/2 (grown when p is outside, shrunk when inside),
 // over which the primitive's |SDF| stays above delta/2 and its sign cannot
-// change; the same for capsules (cylinder and end balls); |d| - delta/2 for
+// change; the same for capsules (cylinder and end balls) and for those three
+// shapes placed by a frame without a domain operation; |d| - delta/2 for
 // soft regions (dsoft) and other shapes; the exit of the bounding box shrunk
 // by delta/2.  The caller moves max(d_min - delta/2,
 // bound).  FP64: the reference's operations in its order.
@@ -789,6 +790,34 @@ static __device__ __noinline__ double seg_capsule64(const double *P, double d, d
     return t > 0.0 ? t : 0.0;
 }
 
+// A sphere, box or capsule placed by a frame without a domain operation:
+// the local ray q + (t / s) w (q = R^T (p - t) / s, w = R^T u) and the local
+// bound with margin dh / s, times s; other frames keep the isotropic bound.
+static __device__ __noinline__ double seg_xprim64(const DevScene &S, int kind, int i, double d, double px,
+                                                  double py, double pz, double ux, double uy, double uz,
+                                                  double dh)
+{
+    const double *X = S.xf64 + kXf64 * i;
+    if ((int)__ldg(X + 13) != 0 || kind > 2) return fabs(d) - dh;
+    const double vx = px - __ldg(X + 9), vy = py - __ldg(X + 10), vz = pz - __ldg(X + 11);
+    const double s = __ldg(X + 12);
+    const double q0 = (__ldg(X) * vx + __ldg(X + 3) * vy + __ldg(X + 6) * vz) / s;
+    const double q1 = (__ldg(X + 1) * vx + __ldg(X + 4) * vy + __ldg(X + 7) * vz) / s;
+    const double q2 = (__ldg(X + 2) * vx + __ldg(X + 5) * vy + __ldg(X + 8) * vz) / s;
+    const double w0 = __ldg(X) * ux + __ldg(X + 3) * uy + __ldg(X + 6) * uz;
+    const double w1 = __ldg(X + 1) * ux + __ldg(X + 4) * uy + __ldg(X + 7) * uz;
+    const double w2 = __ldg(X + 2) * ux + __ldg(X + 5) * uy + __ldg(X + 8) * uz;
+    const double hl = dh / s;
+    const double *P = S.p64 + 8 * i;
+    double t;
+    if (kind == 0) t = seg_sphere64(P, d, q0, q1, q2, w0, w1, w2, hl);
+    else if (kind == 1)
+        t = seg_box64(__ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5), d, q0, q1, q2,
+                      w0, w1, w2, hl);
+    else t = seg_capsule64(P, d, q0, q1, q2, w0, w1, w2, hl);
+    return s * t;
+}
+
 template <bool G>
 static __device__ __noinline__ double segment_bound64(const DevScene &S, double dsoft, double dbox, double px,
                                                       double py, double pz, double ux, double uy, double uz)
@@ -810,8 +839,10 @@ static __device__ __noinline__ double segment_bound64(const DevScene &S, double 
                           py, pz, ux, uy, uz, dh);
         } else if (kind == 2) {
             b = seg_capsule64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, dh);
+        } else if (G && (kind & kXformFlag)) {
+            b = seg_xprim64(S, kind & 0xf, i, d, px, py, pz, ux, uy, uz, dh);
         } else {
-            b = fabs(d) - dh;            // other shapes and placed ones: isotropic
+            b = fabs(d) - dh;            // tori and cylinders: isotropic
         }
         t = fmin(t, b);
     }
@@ -953,6 +984,30 @@ static __device__ __noinline__ float seg_capsule32(float4 A, float4 Bv, float d,
     return t > 0.f ? t : 0.f;
 }
 
+// FP32 placed sphere, box or capsule (frame without a domain operation).
+static __device__ __noinline__ float seg_xprim32(const DevScene &S, int kind, int i, float d, float px, float py,
+                                                 float pz, float ux, float uy, float uz, float dh)
+{
+    const float4 *X = S.xf32 + kXf32 * i;
+    const float4 R0 = __ldg(X), R1 = __ldg(X + 1), R2 = __ldg(X + 2), SC = __ldg(X + 3);
+    if ((int)SC.z != 0 || kind > 2) return fabsf(d) - dh;
+    const float vx = px - R0.w, vy = py - R1.w, vz = pz - R2.w;
+    const float q0 = (R0.x * vx + R0.y * vy + R0.z * vz) * SC.y;
+    const float q1 = (R1.x * vx + R1.y * vy + R1.z * vz) * SC.y;
+    const float q2 = (R2.x * vx + R2.y * vy + R2.z * vz) * SC.y;
+    const float w0 = R0.x * ux + R0.y * uy + R0.z * uz;
+    const float w1 = R1.x * ux + R1.y * uy + R1.z * uz;
+    const float w2 = R2.x * ux + R2.y * uy + R2.z * uz;
+    const float hl = dh * SC.y;
+    const float4 A = (*(S.p32 + 2 * i)), B = (*(S.p32 + 2 * i + 1));
+    float t;
+    if (kind == 0) t = seg_sphere32(A, d, q0, q1, q2, w0, w1, w2, hl);
+    else if (kind == 1)
+        t = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, q0, q1, q2, w0, w1, w2, 1.0f / w0, 1.0f / w1, 1.0f / w2, hl);
+    else t = seg_capsule32(A, B, d, q0, q1, q2, w0, w1, w2, hl);
+    return SC.x * t;
+}
+
 template <bool G>
 static __device__ __noinline__ float segment_bound32(const DevScene &S, float dsoft, float dbox, float px,
                                                      float py, float pz, float ux, float uy, float uz)
@@ -974,6 +1029,8 @@ static __device__ __noinline__ float segment_bound32(const DevScene &S, float ds
             b = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, px, py, pz, ux, uy, uz, iux, iuy, iuz, dh);
         } else if (kind == 2) {
             b = seg_capsule32((*(S.p32 + 2 * i)), (*(S.p32 + 2 * i + 1)), d, px, py, pz, ux, uy, uz, dh);
+        } else if (G && (kind & kXformFlag)) {
+            b = seg_xprim32(S, kind & 0xf, i, d, px, py, pz, ux, uy, uz, dh);
         } else {
             b = fabsf(d) - dh;
         }
