@@ -49,8 +49,8 @@ MUTANTS = [
      "if (S->stepping == 1) L = fmin(L, segment_bound(S, &E, p, u));"),
     ("torus_tube_radius", "return sqrt(ring * ring + dz * dz) - q[4];", "return sqrt(ring * ring + dz * dz) - q[3];"),
     ("cylinder_cap", "double b = fabs(dz) - q[4];", "double b = dz - q[4];"),
-    ("frame_rotation_transposed", "q[0] = (X->rot[0] * vx + X->rot[3] * vy + X->rot[6] * vz) / X->s;",
-     "q[0] = (X->rot[0] * vx + X->rot[1] * vy + X->rot[2] * vz) / X->s;"),
+    ("frame_rotation_transposed", "double q[3];\n    q[0] = (X->rot[0] * vx + X->rot[3] * vy + X->rot[6] * vz) / X->s;",
+     "double q[3];\n    q[0] = (X->rot[0] * vx + X->rot[1] * vy + X->rot[2] * vz) / X->s;"),
     ("frame_scale_dropped", "return X->s * sdf_base(pr->kind, pr->p, q) / L;", "return sdf_base(pr->kind, pr->p, q) / L;"),
     ("elongate_clamp", "q[a] = q[a] - fmin(fmax(q[a], -X->a[a]), X->a[a]);", "q[a] = q[a] - fmin(q[a], X->a[a]);"),
     ("repeat_rounding", "double k = floor(q[a] / c + 0.5);", "double k = floor(q[a] / c);"),
