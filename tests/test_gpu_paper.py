@@ -116,3 +116,28 @@ def test_table1_penetration_depth_gpu(ctx, row):
     # energy closes: R + T + A + killed - gain = packets
     bal = (t["R"] + t["T"] + t["A"] + t["killed"] - t["gain"]) / FX
     assert abs(bal - wl.npackets) < 1e-4 * wl.npackets
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_glass_sphere_ball_lens_focus_gpu(ctx, precision):
+    # the smooth-surface test of Sec. 3.2: the clear glass sphere (n = 1.46,
+    # R = 1 cm) focuses a narrow axial beam at nR / (2 (n - 1)) from its
+    # centre; FP64 also equals the oracle bit for bit
+    n, R = 1.46, 1.0
+    z_focus = -1.0 - n * R / (2.0 * (n - 1.0))
+    grid = W.Grid((0.498, -0.002, -3.0), (0.502, 0.002, -2.2), (1, 1, 160))
+    npk = 4_000_000 if precision == "mixed" else 1_000_000
+    wl = W.glass_sphere_beam(npk, beam_radius=0.1, grid=grid, precision=precision).with_stepping(W.SEGMENT)
+    flu, t = run_gpu(ctx, wl, precision)
+    assert t["packets"] == npk and t["max_steps_hit"] == 0
+    assert t["A"] == 0 and t["R"] + t["T"] == npk * 2 ** 32
+    col = flu[:, 0, 0].astype(np.float64)
+    z = -3.0 + (np.arange(160) + 0.5) * 0.005
+    half = z[col > 0.5 * col.max()]
+    mid = 0.5 * (half.min() + half.max())
+    assert abs(mid - z_focus) < 0.015, (precision, mid, z_focus)
+    if precision == "fp64":
+        fo, to, _ = O.run(wl)
+        assert np.array_equal(flu, fo)
+        for k in ("R", "T", "A", "killed", "gain", "packets", "scatters", "steps"):
+            assert t[k] == to[k], k

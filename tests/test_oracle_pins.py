@@ -1077,3 +1077,24 @@ def test_segment_stepping_same_transport_fewer_steps(factory):
     pb = r1["R"] + r1["T"] + r1["A"] + r1["killed"] - r1["gain"]
     assert np.all(np.abs(pb - FX) <= 0.5 * (r1["scatters"] + 3) + 1)
     assert t1["steps"] < 0.7 * t0["steps"]
+
+
+def test_glass_sphere_focuses_at_the_ball_lens_focal_length():
+    # The clear glass sphere of Sec. 3.2 (n = 1.46, radius 1 cm) is a ball
+    # lens: a narrow beam along its axis focuses at nR / (2 (n - 1)) from the
+    # centre (paraxial optics, two refractions at the spherical surface).  The
+    # fluence in a thin column on the axis is largest where the beam is
+    # narrowest; the midpoint of its half-maximum span is the focus.
+    n, R = 1.46, 1.0
+    z_focus = -1.0 - n * R / (2.0 * (n - 1.0))
+    grid = W.Grid((0.498, -0.002, -3.0), (0.502, 0.002, -2.2), (1, 1, 160))
+    wl = W.glass_sphere_beam(1_000_000, beam_radius=0.1, grid=grid, precision="fp64")
+    flu, tot, _ = O.run(wl)
+    col = flu[:, 0, 0].astype(np.float64)
+    z = -3.0 + (np.arange(160) + 0.5) * 0.005
+    half = z[col > 0.5 * col.max()]
+    mid = 0.5 * (half.min() + half.max())
+    assert abs(mid - z_focus) < 0.015, (mid, z_focus)
+    # nothing absorbs in clear glass and air: every packet is reflected or
+    # transmitted
+    assert tot["A"] == 0 and tot["R"] + tot["T"] == wl.npackets * 2 ** 32

@@ -287,6 +287,23 @@ def glass_container(npackets: int = 100_000_000, seed: int = 5, precision: str =
                     npackets, seed, precision)
 
 
+def glass_sphere_beam(npackets: int = 27_000_000, seed: int = 9, precision: str = "mixed",
+                      beam_radius: float = 0.3, grid_n: int = 200, grid=None) -> Workload:
+    """The smooth-surface test of Sec. 3.2 (Fig. 5): a clear glass sphere
+    (n = 1.46, radius 1 cm) centred at (0.5, 0, -1) cm in air, lit from above
+    by a uniform disc beam of radius 0.3 cm along the sphere's axis; about
+    2.7e7 photons.  The paper leaves the medium's extent, the grid and the
+    beam profile open: the bounding box holds the sphere and its focal region
+    below, and the grid covers the bounding box at grid_n^3 unless given."""
+    prims = (Prim(SPHERE, (0.5, 0.0, -1.0, 1.0)),)
+    regions = (Region(prim_program([0]), 0.0, 0.0, 0.0, 1.46),)
+    lo, hi = (-1.5, -2.0, -4.0), (2.5, 2.0, 0.5)
+    scene = Scene(prims, regions, 1.0, lo, hi)
+    g = grid if grid is not None else Grid((-1.5, -2.0, -4.0), (2.5, 2.0, 0.0), (grid_n, grid_n, grid_n))
+    return Workload(f"glass_sphere_beam_{npackets:.0e}".replace("+0", ""), scene,
+                    Source(DISC, (0.5, 0.0, 0.25), (0.0, 0.0, -1.0), beam_radius), g, npackets, seed, precision)
+
+
 def served_mix(njobs: int = 200, seed: int = 4, budget_lo: float = 1e4, budget_hi: float = 1e7,
                stepping: str = SPHERE_TRACING):
     """Served mix: jobs drawn from the four scene families with optics redrawn
