@@ -22,9 +22,9 @@
  *     (Sec. 3.1) with Russian roulette,
  *   - track-length fluence in rectangular voxel bins      (Sec. 3.1-3.2).
  *
- * Readings of points the paper leaves open (xi in (0,1], delta, normal
- * step, push-off, Fresnel form, roulette constants, RNG) are the ones
- * stated in the build's design notes; each is repeated at its use below.
+ * Points the paper leaves open (xi in (0,1], delta, normal step, push-off,
+ * Fresnel form, roulette constants, RNG) take one reading each, stated at
+ * its use below.
  *
  * Bit-reproducibility conventions: IEEE +,-,*,/,sqrt only, compiled with
  * -ffp-contract=off, fixed expression order; ln and sin/cos are written

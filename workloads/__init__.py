@@ -162,7 +162,7 @@ def splitmix64(x: int) -> int:
 
 
 # ---------------------------------------------------------------------------
-# The five workloads.  Concrete numbers are this build's synthetic stand-ins
+# The five workloads.  Their concrete numbers are synthetic stand-ins
 # for the scenes the paper describes (vessel network Sec. 4, glass bottle
 # Sec. 4 / Fig. 7, layered tissue as in the Jacques slab of Sec. 3.1).
 # ---------------------------------------------------------------------------
