@@ -1098,3 +1098,30 @@ def test_glass_sphere_focuses_at_the_ball_lens_focal_length():
     # nothing absorbs in clear glass and air: every packet is reflected or
     # transmitted
     assert tot["A"] == 0 and tot["R"] + tot["T"] == wl.npackets * 2 ** 32
+
+
+def test_capsule_bound_safe_for_rays_nearly_parallel_to_the_axis():
+    # the cylinder part's quadratic is worst conditioned when the ray runs
+    # almost along the axis, close to the wall: brute force along the move,
+    # from inside and from outside, at angles down to 1e-9 rad
+    d = 1e-6
+    r = 0.05
+    cap = W.Scene((W.Prim(W.CAPSULE, (0.0, 0.0, -1.0, 0.0, 0.0, 1.0, r)),),
+                  (W.Region(W.prim_program([0]), 0.0, 1.0, 0.0, 1.5),), 1.0,
+                  (-2, -2, -3), (2, 2, 3), delta=d, stepping=W.SEGMENT)
+    checked = 0
+    for off in (r - 4 * d, r - 1e-3, r + 4 * d, r + 1e-3):      # inside and outside the wall
+        for ang in (0.0, 1e-9, 1e-6, 1e-4, 1e-2):
+            for sgn in (1.0, -1.0):                              # towards and away from the wall
+                p = np.array([off, 0.0, -0.5])
+                u = np.array([sgn * math.sin(ang), 0.0, math.cos(ang)])
+                if abs(O.region_sdf(cap, 0, p)) <= d:
+                    continue
+                t = O.segment_step(cap, p, u)
+                s0 = np.sign(O.region_sdf(cap, 0, p))
+                for s in np.linspace(0.0, t, 400):
+                    q = p + s * u
+                    v = O.region_sdf(cap, 0, q)
+                    assert np.sign(v) == s0 and abs(v) >= d / 2 - 1e-12, (off, ang, sgn, t, s, v)
+                checked += 1
+    assert checked == 40
