@@ -424,6 +424,32 @@ def main():
     value = args.packets * args.steps * world / t_sum
     kernel_s = t_sum / args.steps   # per-step device time ~ the packet kernel (one launch)
 
+    e2e_multi = None
+    if dist and not args.quick:
+        # end to end at N GPUs: every rank makes the public synchronous call
+        # with host buffers, on its own seed (independent packets); the
+        # slowest rank sets the time
+        from dataclasses import replace as dc_replace
+        wl_rank = dc_replace(wl, seed=wl.seed + 1000 * rank)
+        h_flu = np.zeros((g.n[2], g.n[1], g.n[0]), dtype=np.int64)
+        ctx.run(wl_rank.with_packets(100_000), args.precision, out=h_flu)
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ctx.run(wl_rank, args.precision, out=h_flu)
+        tt = torch.tensor([(time.perf_counter() - t0) / 3], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        m = smc.Marshalled(wl.scene, wl.source, wl.grid)
+        import ctypes as C
+        h2d = (C.sizeof(m.scene) + C.sizeof(m.prims) + C.sizeof(m.nodes) + C.sizeof(m.regions)
+               + C.sizeof(m.source) + C.sizeof(m.grid))
+        e2e_multi = {"value": args.packets * world / float(tt.item()), "unit": UNIT,
+                     "h2d_bytes_per_step": int(h2d) * world,
+                     "d2h_bytes_per_step": int(h_flu.nbytes + C.sizeof(smc.Totals)) * world,
+                     "api": "smcrt_run with host scene structs and a host fluence buffer, on every rank "
+                            "(seed + 1000 rank), slowest rank"}
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -503,7 +529,9 @@ def main():
         p.close()
         return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / nsteps, smc.totals_from_tensor(tot), flu.cpu().numpy()
 
-    if not args.quick:
+    if e2e_multi is not None:
+        out["e2e"] = e2e_multi
+    if not args.quick and world == 1:
         # ---- mixed precision with plain sphere tracing (the paper's step) ---
         totals_st = None
         if args.stepping != W.SPHERE_TRACING and args.precision == "mixed":
