@@ -36,6 +36,12 @@ MUTANTS = [
     ("tau_consumed", "tau = tau - mu_t * L;", "tau = tau - mu_a * L;"),
     ("absorbed_weight", "double wn = w * (mu_s / mu_t);", "double wn = w * (mu_a / mu_t);"),
     ("roulette_gain", "P.gain += fx(w * (OR_ROULETTE_M - 1.0));", "P.gain += fx(w * OR_ROULETTE_M);"),
+    # survival chance not matched to the weight multiplier: the energy
+    # identity still holds, only the roulette pin's expectation catches these
+    ("roulette_survival_mismatch", "if (xi[2] <= 1.0 / OR_ROULETTE_M) {", "if (xi[2] <= 0.2) {"),
+    ("roulette_survival_slight", "if (xi[2] <= 1.0 / OR_ROULETTE_M) {", "if (xi[2] <= 0.09) {"),
+    ("roulette_survival_side", "if (xi[2] <= 1.0 / OR_ROULETTE_M) {", "if (xi[2] > 1.0 / OR_ROULETTE_M) {"),
+    ("roulette_threshold", "if (w < OR_W_ROULETTE) {", "if (w < 10.0 * OR_W_ROULETTE) {"),
     ("escape_split", "if (u[0] * src->dir[0] + u[1] * src->dir[1] + u[2] * src->dir[2] < 0.0) P.R += fx(w);",
      "if (u[0] * src->dir[0] + u[1] * src->dir[1] + u[2] * src->dir[2] > 0.0) P.R += fx(w);"),
     ("region_priority", "if (d < 0.0) E.region = r;", "if (d < 0.0 && E.region < 0) E.region = r;"),

@@ -691,6 +691,44 @@ def test_energy_conservation(factory):
     assert np.all(np.abs(pb - FX) <= 0.5 * (rec["scatters"] + 3) + 1)
 
 
+def test_roulette_is_unbiased():
+    # Russian roulette below the weight threshold (Sec. 2.1 reuses the
+    # earlier codes' absorption routine; threshold 1e-4, survival 1/m with
+    # weight x m) must not change the expected energy: a survivor gains
+    # w (m - 1) with probability 1/m, a loser is killed with w with
+    # probability 1 - 1/m, both w (m - 1) / m in expectation -- equal only
+    # when the survival chance and the multiplier match.  In a medium that
+    # no packet leaves (albedo 0.9, mean free path 1e-3 cm, 1 cm from the
+    # surface), every packet meets roulette and all of its weight is
+    # absorbed in expectation: E[A] = 1, i.e. E[killed - gain] = 0 per
+    # packet.  The energy identity R + T + A + killed - gain = 1 holds for
+    # any survival threshold, so only this expectation pins it.
+    mu_a, mu_s = 100.0, 900.0
+    sc = W.Scene((W.Prim(W.SPHERE, (0.0, 0.0, 0.0, 1.0)),),
+                 (W.Region(W.prim_program([0]), mu_a, mu_s, 0.0, 1.0),), 1.0,
+                 (-1.1, -1.1, -1.1), (1.1, 1.1, 1.1))
+    n = 20000
+    _, tot, rec = _run(sc, W.Source(W.ISO_POINT, (0, 0, 0), (0, 0, -1)), n, 41, fluence=False, records=True)
+    assert tot["R"] == 0 and tot["T"] == 0 and tot["max_steps_hit"] == 0
+    killed = rec["killed"].astype(np.float64) / FX
+    gain = rec["gain"].astype(np.float64) / FX
+    # every packet ends in a roulette kill of a weight below the threshold
+    assert np.all(rec["killed"] > 0) and np.all(killed < 1e-4)
+    # survivors: each gain is (m - 1) w with w below the threshold; about one
+    # survival in nine roulette events, so the 2e4 kills come with ~2.2e3
+    # survivals -- over 2.2e4 roulette events in all
+    events = n + np.count_nonzero(gain)
+    assert events > 2.1e4 and np.all(gain < 9e-3)
+    d = killed - gain
+    z = d.mean() / (d.std() / math.sqrt(n))
+    assert abs(z) < 3.0, (d.mean(), d.std(), z)
+    # the expected kill per packet is the closed form of the first roulette
+    # event: with no survivors the packet dies with w = 0.9^k < 1e-4
+    k = math.ceil(math.log(1e-4) / math.log(mu_s / (mu_a + mu_s)))
+    w_first = (mu_s / (mu_a + mu_s)) ** k
+    assert abs(np.median(killed[gain == 0]) - w_first) < 1e-9
+
+
 def test_thread_count_independence():
     wl = W.sphere_pencil(600)
     f1, t1, _ = O.run(wl, threads=1)
