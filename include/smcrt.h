@@ -319,7 +319,10 @@ int smcrt_plan_autotune(smcrt_plan *plan, uint64_t trial_packets, int32_t *block
  * exits.  Scenes are limited accordingly: at most 128 primitives, 256 CSG
  * nodes and 16 regions (larger ones return SMCRT_ERR_NO_MEMORY; invalid ones
  * SMCRT_ERR_BAD_SCENE or SMCRT_ERR_BAD_ARG).  It calls no cudaMalloc or
- * cudaFree and allocates no host memory.
+ * cudaFree and allocates no host memory: the scene is compiled into a fixed
+ * host buffer (calls from several host threads take turns on it) and reaches
+ * the device array in the launch arguments of small copy kernels, so nothing
+ * reads the caller's or the library's host memory after the call returns.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any

@@ -7,6 +7,8 @@
 // address: the address is looked up once per device with
 // cudaGetSymbolAddress and cached.  Every call shares the array and leaves
 // its contents behind, so calls that overlap on the GPU race with one another.
+// The image is written into the array by small copy kernels that carry it in
+// their launch arguments, so the call reads no host memory after it returns.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -29,10 +31,27 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 unsigned char *g_scratch_addr[kNoAllocMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-// Host staging of the scene image (thread-local, fixed size: no allocation
-// at call time).  cudaMemcpyAsync from pageable memory stages the bytes
-// before it returns, so the buffer can be reused by the next call.
-thread_local unsigned char t_image[kNoAllocScratchBytes];
+// Host staging of the scene image: one file-scope buffer, used under
+// g_image_mu from the start of the image build until the last copy kernel
+// has been launched.  The image reaches the device as the parameters of
+// copy kernels (below): launch arguments are copied when the kernel is
+// launched, so the buffer is free again as soon as the launches return and
+// no copy reads host memory later.
+alignas(16) unsigned char g_image[kNoAllocScratchBytes];
+std::mutex g_image_mu;
+
+// Bytes of the image carried by one copy kernel's parameters.
+constexpr int kChunkBytes = 8192;
+struct ImageChunk {
+    uint32_t nwords;          // 16-byte words in this chunk
+    uint32_t pad[3];
+    uint4 w[kChunkBytes / 16];
+};
+
+__global__ void __launch_bounds__(256) copy_image_chunk(uint4 *dst, const ImageChunk c)
+{
+    for (uint32_t k = threadIdx.x; k < c.nwords; k += blockDim.x) dst[k] = c.w[k];
+}
 
 constexpr size_t kJobOff = 0;
 constexpr size_t kStatusOff = 256;
@@ -280,14 +299,25 @@ extern "C" int smcrt_run_noalloc(const smcrt_scene *scene, const smcrt_source *s
     unsigned char *base = nullptr;
     int rc = scratch_address(&base);
     if (rc != SMCRT_OK) return rc;
-    size_t used = 0;
-    rc = build_image(scene, source, grid, precision, base, t_image, &used);
-    if (rc != SMCRT_OK) return rc;
-    if (npackets == 0) return SMCRT_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    // the image and a cleared status word; the descriptor goes in by value
-    if (cudaMemcpyAsync(base + kImageOff, t_image, used, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return SMCRT_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_image_mu);
+        size_t used = 0;
+        rc = build_image(scene, source, grid, precision, base, g_image, &used);
+        if (rc != SMCRT_OK) return rc;
+        if (npackets == 0) return SMCRT_OK;
+        // the image (a multiple of 16 bytes), chunk by chunk, in the copy
+        // kernels' launch arguments
+        static ImageChunk chunk;   // guarded by g_image_mu
+        for (size_t o = 0; o < used; o += kChunkBytes) {
+            const size_t nb = used - o < (size_t)kChunkBytes ? used - o : (size_t)kChunkBytes;
+            chunk.nwords = (uint32_t)(nb / 16);
+            std::memcpy(chunk.w, g_image + o, nb);
+            copy_image_chunk<<<1, 256, 0, s>>>((uint4 *)(base + kImageOff + o), chunk);
+            if (cudaGetLastError() != cudaSuccess) return SMCRT_ERR_CUDA;
+        }
+    }
+    // a cleared status word; the descriptor goes in by value
     if (cudaMemsetAsync(base + kStatusOff, 0, sizeof(int), s) != cudaSuccess) return SMCRT_ERR_CUDA;
     JobWork jw{};
     jw.next = id_begin;
