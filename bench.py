@@ -39,25 +39,44 @@ METRIC = "photon packets/s (and p50/p99 job latency) mixed vs plain FP64 at equa
 UNIT = "packets/s"
 FX = 2.0 ** 32
 
-# Algorithmic FP32 work per counted event of the mixed kernel (operations,
-# an FMA counted as 2), from the arithmetic of the kernel source:
-#   box SDF 22 (3 sub, 3 abs, 3 sub, 3 max, 5 for the squared norm, sqrt,
-#   3 min/max, add); region bookkeeping 5 per region (compare, abs, compare,
-#   2 selects); bounding box = one box SDF;
-#   step: tally set-up 40 + move 6 + tau update 2;  voxel piece 16;
+# Algorithmic FP32 work per counted event (operations, an FMA counted as 2),
+# from the arithmetic of the method; the event counts come from the FP64
+# oracle's own counters on a sample of the same workload and step rule.
+#   primitive SDF: sphere 8, box 20 (3 sub, 3 abs, 3 sub, 3 max, 5 for the
+#   squared norm, sqrt, min/max), capsule 22, torus 12, cylinder 14;
+#   smooth union 8; per scene evaluation: the bounding box 20 and 5 per
+#   region (compare, abs, compare, 2 selects);
+#   step: tally set-up 40 + move 6 + tau update 2 = 48;  voxel piece 16;
 #   interaction: weight 3, HG 12, azimuth sincos 4, basis 14, rotation 15,
-#   normalisation 8, roulette 2, log 4 = 62.
-FLOPS_BOX = 22
+#   normalisation 8, roulette 2, log 4 = 62;  interface (normal from the
+#   gradient, Fresnel / Snell cosines and directions) 30;
+#   segment-stepping bound, per move that used it: the bounding box's ray
+#   exit 30, plus per primitive ray bound sphere 15, box 30, capsule 60.
+FLOPS_PRIM = {"sphere": 8, "box": 20, "capsule": 22, "torus": 12, "cylinder": 14}
+FLOPS_SMOOTH = 8
+FLOPS_BBOX = 20
 FLOPS_REGION = 5
 FLOPS_STEP = 48
 FLOPS_PIECE = 16
 FLOPS_INTERACTION = 62
+FLOPS_INTERFACE = 30
+FLOPS_SEG_BBOX = 30
+FLOPS_SEG_PRIM = {"sphere": 15, "box": 30, "capsule": 60, "torus": 0, "cylinder": 0}
 
 
-def three_layer_flops(t: dict) -> float:
-    per_eval = 3 * FLOPS_BOX + 3 * FLOPS_REGION + FLOPS_BOX
-    return (t["scene_evals"] * per_eval + t["steps"] * FLOPS_STEP + t["pieces"] * FLOPS_PIECE
-            + t["scatters"] * FLOPS_INTERACTION)
+def algorithmic_work(t: dict, nregions: int) -> dict:
+    """FP32 flops and int64 atomics per packet from the oracle's counters
+    ``t`` (totals of a sample): the roofline's algorithmic work."""
+    n = max(1, t["packets"])
+    prim = sum(t[f"prim_{k}"] * w for k, w in FLOPS_PRIM.items())
+    seg_per_call = FLOPS_SEG_BBOX + (sum(t[f"seg_{k}"] * w for k, w in FLOPS_SEG_PRIM.items())
+                                     / max(1, t["seg_calls"]))
+    flops = (prim + t["smooth_ops"] * FLOPS_SMOOTH + t["scene_evals"] * (FLOPS_BBOX + FLOPS_REGION * nregions)
+             + t["steps"] * FLOPS_STEP + t["pieces"] * FLOPS_PIECE + t["scatters"] * FLOPS_INTERACTION
+             + t["interfaces"] * FLOPS_INTERFACE + t["seg_moves"] * seg_per_call)
+    return {"flops_per_packet": flops / n, "atomics_per_packet": t["pieces"] / n,
+            "counts_per_packet": {k: t[k] / n for k in ("steps", "scene_evals", "prim_evals", "scatters",
+                                                        "interfaces", "pieces", "seg_moves")}}
 
 
 KERNEL_SOURCES = ["paper_2112_08035_gb300/csrc/smcrt_kernel.cuh", "paper_2112_08035_gb300/csrc/smcrt_k32.cu",
@@ -160,11 +179,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-def oracle_sample(wl, seconds: float, id_base: int = 0):
+def oracle_sample(wl, seconds: float, id_base: int = 0, K: int = 10, block=(10, 10, 10)):
     """Time the FP64 oracle, as it stands, on a bounded sample sized to take
-    about ``seconds``, run as two halves of consecutive ids; returns
-    (packets/s, packets, threads, per-packet records, the halves' fluence
-    maps)."""
+    about ``seconds``, run as K batches of consecutive ids; returns a dict:
+    packets/s, packets, threads, per-packet records, the first and second
+    halves' fluence maps, per-batch fluence block sums (per packet) and the
+    oracle's totals (its work counters included)."""
     import numpy as np
     import oracle as O
     threads = os.cpu_count() or 1
@@ -172,12 +192,21 @@ def oracle_sample(wl, seconds: float, id_base: int = 0):
     t0 = time.perf_counter()
     O.run(wl.with_packets(n0), id_base, id_base + n0, threads=threads, fluence=True)
     rate0 = n0 / (time.perf_counter() - t0)
-    h = int(max(n0, min(5_000_000, rate0 * seconds))) // 2
+    per = int(max(n0, min(5_000_000, rate0 * seconds))) // K
+    recs, blocks, maps = [], [], []
+    tot = None
     t0 = time.perf_counter()
-    f1, _, r1 = O.run(wl.with_packets(h), id_base, id_base + h, threads=threads, records=True)
-    f2, _, r2 = O.run(wl.with_packets(h), id_base + h, id_base + 2 * h, threads=threads, records=True)
+    for k in range(K):
+        f, t, r = O.run(wl.with_packets(per), id_base + k * per, threads=threads, records=True)
+        recs.append(r)
+        maps.append(f)
+        blocks.append(block_sums(f, block) / FX / per)
+        tot = t if tot is None else {key: tot[key] + t[key] for key in tot}
     dt = time.perf_counter() - t0
-    return 2 * h / dt, 2 * h, threads, np.concatenate([r1, r2]), (f1, f2)
+    h = K // 2
+    return {"pps": K * per / dt, "packets": K * per, "threads": threads, "records": np.concatenate(recs),
+            "halves": (sum(maps[:h]), sum(maps[h:2 * h])), "half_packets": h * per,
+            "blocks": np.array(blocks), "totals": tot}
 
 
 def fluence_l2(gpu_flu, n_gpu: int, halves, n_half: int) -> dict:
@@ -195,6 +224,122 @@ def fluence_l2(gpu_flu, n_gpu: int, halves, n_half: int) -> dict:
     noise = float(np.linalg.norm(f1 - f2)) / 2.0 / norm
     return {"fluence_rel_l2": l2, "fluence_oracle_noise_rel_l2": noise,
             "fluence_l2_over_noise": l2 / noise if noise > 0 else None}
+
+
+def _z_from_t(t, dof):
+    """Normal deviate with the same two-sided tail probability as Student's t
+    with ``dof`` degrees of freedom (batch means: the spread is estimated)."""
+    from scipy import stats
+    t = np.asarray(t, dtype=np.float64)
+    return np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), dof))
+
+
+def paired_z(a, b) -> float:
+    """z of the mean of paired differences a - b (same packet ids or the same
+    batches on both sides), from the differences' own spread."""
+    d = np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)
+    se = d.std(ddof=1) / math.sqrt(d.size)
+    return float(d.mean() / se) if se > 0 else (0.0 if d.mean() == 0 else math.inf)
+
+
+def paired_block_stats(A, B, k: float = 3.0) -> dict:
+    """Block-by-block comparison of two fluence estimates made on the same
+    K batches of packet ids (A, B: (K, nblocks) per-batch block sums); see
+    ``block_stats``."""
+    return block_stats(A, B, paired=True, k=k)
+
+
+def block_stats(A, B, paired: bool = True, k: float = 3.0) -> dict:
+    """Block-by-block comparison of two fluence estimates.  A and B are
+    (K_a, nblocks) and (K_b, nblocks) arrays of per-batch block sums,
+    normalised per packet.  Paired (K_a = K_b, the same packet ids in batch
+    i on both sides): the t statistic of the mean difference over the K
+    batches, K - 1 degrees of freedom.  Unpaired (independent samples): the
+    Welch t of the two batch means, Welch-Satterthwaite degrees of freedom.
+    Blocks are tested where every batch on both sides is non-zero (each batch
+    sum then adds many packets, so it is close to normal).  Each t becomes the
+    normal deviate z of the same two-sided tail.  Under equal expectations
+    every z is standard normal, so with n blocks tested:
+      - the count of |z| > k is binomial(n, p_k) for independent blocks:
+        accepted up to its mean plus 3 standard deviations (the variance
+        widened by n / n_eff, below);
+      - chi2/dof = mean(z^2) has mean 1 and standard deviation sqrt(2/n)
+        for independent blocks: accepted within 1 +- 3 sqrt(2 / n_eff),
+        where n_eff is n divided by 1 + (n - 1) times the blocks' mean squared
+        correlation (blocks crossed by the same packets are correlated);
+      - max |z| stays below the deviate of a two-sided tail p_k / n (a
+        Bonferroni bound, valid whatever the correlation)."""
+    from scipy import stats
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    ok = np.all(A > 0, axis=0) & np.all(B > 0, axis=0)
+    A, B = A[:, ok], B[:, ok]
+    n = int(A.shape[1])
+    if n == 0:
+        return {"blocks": 0, "pass": False}
+    if paired:
+        K = A.shape[0]
+        D = A - B
+        m = D.mean(axis=0)
+        v = D.var(axis=0, ddof=1) / K
+        dof = np.full(n, K - 1.0)
+        dev = (D - m) / math.sqrt(K)          # per-batch deviations of the mean difference
+        kk = K
+    else:
+        Ka, Kb = A.shape[0], B.shape[0]
+        va, vb = A.var(axis=0, ddof=1) / Ka, B.var(axis=0, ddof=1) / Kb
+        m = A.mean(axis=0) - B.mean(axis=0)
+        v = va + vb
+        with np.errstate(divide="ignore", invalid="ignore"):
+            dof = np.where(v > 0, v * v / (va * va / (Ka - 1) + vb * vb / (Kb - 1)), 1.0)
+        dev = None
+        kk = min(Ka, Kb)
+    se = np.sqrt(v)
+    t = np.where(se > 0, m / np.where(se > 0, se, 1.0), 0.0)
+    z = _z_from_t(t, np.maximum(dof, 1.0))
+    p_k = 2.0 * stats.norm.sf(k)
+    n_out = int(np.count_nonzero(np.abs(z) > k))
+    # effective number of independent blocks: from the correlation matrix of
+    # the blocks' mean differences, estimated from the batches
+    if n > 1 and kk > 2:
+        if paired:
+            C = dev.T @ dev / (kk - 1)
+        else:
+            da = (A - A.mean(axis=0)) / A.shape[0]
+            db = (B - B.mean(axis=0)) / B.shape[0]
+            C = da.T @ da * (A.shape[0] / (A.shape[0] - 1)) + db.T @ db * (B.shape[0] / (B.shape[0] - 1))
+        d = np.sqrt(np.clip(np.diag(C), 1e-300, None))
+        R = C / d[:, None] / d[None, :]
+        r2 = (np.sum(R * R) - n) / (n * (n - 1))
+        # the sample correlation of unrelated blocks is itself ~1/(K-1) in square
+        r2 = max(0.0, r2 - 1.0 / (kk - 1))
+        n_eff = n / (1.0 + (n - 1) * r2)
+    else:
+        n_eff = float(n)
+    # correlated blocks also widen the spread of the count (by n / n_eff)
+    out_limit = n * p_k + 3.0 * math.sqrt(n * p_k * (1.0 - p_k) * n / n_eff)
+    chi2 = float(np.mean(z * z))
+    chi2_band = 3.0 * math.sqrt(2.0 / n_eff)
+    zmax = float(np.max(np.abs(z)))
+    zmax_limit = float(stats.norm.isf(p_k / 2.0 / n))
+    worst = int(np.nonzero(ok)[0][int(np.argmax(np.abs(z)))])
+    return {"blocks": n, "paired": paired, "n_over_k": n_out, "n_over_k_limit": out_limit,
+            "chi2_dof": chi2, "chi2_band": chi2_band, "n_eff": n_eff, "z_max": zmax,
+            "z_max_limit": zmax_limit, "z_max_block": worst,
+            "z_max_block_rel_diff": float(m[np.argmax(np.abs(z))] / max(abs(B[:, np.argmax(np.abs(z))].mean()), 1e-300)),
+            "pass": bool(n_out <= out_limit and abs(chi2 - 1.0) <= chi2_band and zmax <= zmax_limit)}
+
+
+def block_sums(flu, b):
+    """Sums of a [nz][ny][nx] fluence map over b[0] x b[1] x b[2] voxel blocks
+    (x, y, z block edges), flattened (torch tensor on the device or numpy)."""
+    nz, ny, nx = flu.shape
+    bx, by, bz = b
+    f = flu[: nz // bz * bz, : ny // by * by, : nx // bx * bx]
+    shape = (nz // bz, bz, ny // by, by, nx // bx, bx)
+    if hasattr(f, "data_ptr"):
+        return f.reshape(shape).sum(dim=(1, 3, 5)).double().cpu().numpy().ravel()
+    return f.reshape(shape).sum(axis=(1, 3, 5)).astype(np.float64).ravel()
 
 
 def reference_arm(args):
@@ -352,8 +497,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--packets", type=int, default=10_000_000)
-    ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--serve-jobs", type=int, default=100)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--no-configs", action="store_true", help="skip the configs 0, 2, 3 block")
+    ap.add_argument("--cfg-steps", type=int, default=2, help="timed steps of the 1e8-packet configs")
+    ap.add_argument("--cfg-fp64-packets", type=int, default=1_000_000,
+                    help="FP64 packets timed, and compared, on configs 2 and 3")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="kernel legs only (profiling runs)")
     ap.add_argument("--no-paper-cases", action="store_true", help="skip the paper's Table 2 timing cases")
@@ -420,7 +569,6 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_sum = float(tt.item())
     totals_mixed = smc.totals_from_tensor(tot)
-    flu_legs = {"mixed": flu.cpu().numpy()}   # the last timed step's map (1e7 packets)
     value = args.packets * args.steps * world / t_sum
     kernel_s = t_sum / args.steps   # per-step device time ~ the packet kernel (one launch)
 
@@ -473,7 +621,24 @@ def main():
            "gpu_launches": 2 * args.steps,
            "clocks": clk.summary()}
 
-    # ---- roofline of the packet kernel (ALU-bound: FP32 issue) -----------
+    log(f"mixed {value:.3e} packets/s")
+    import oracle as O
+    # ---- the oracle on a bounded sample of the same workload: the CPU
+    # baseline, the reference for the accuracy fields, and the algorithmic
+    # work counts of the roofline
+    if args.quick or world > 1:
+        counts = O.run(wl.with_packets(20_000), fluence=False)[1]
+        osamp = None
+    else:
+        log("oracle leg")
+        osamp = oracle_sample(wl, args.oracle_seconds, id_base=0)
+        counts = osamp["totals"]
+        out["cpu_baseline"] = {"value": osamp["pps"], "unit": UNIT, "cores": osamp["threads"], "kind": "oracle",
+                               "sample": f"{osamp['packets']} packets (ids 0..{osamp['packets'] - 1}) of the same "
+                                         f"three_layer_slab workload ({args.stepping} stepping), FP64, "
+                                         f"{osamp['threads']} threads, 10 batches"}
+
+    # ---- roofline of the packet kernel: FP32 issue and L2 int64 atomics ----
     peaks, src = load_peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = out["clocks"]["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1455.0
@@ -481,22 +646,30 @@ def main():
     # measured ceilings: the library's FMA and int64-atomic microbenchmarks
     mb = smc.microbench(local)
     peak_tflops = mb["fp32_flops"] / 1e12
-    flops = three_layer_flops(totals_mixed)
-    achieved = flops / kernel_s / 1e12
-    atomics = totals_mixed["pieces"] / kernel_s
-    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                       "frac": achieved / peak_tflops, "traffic": recorded_traffic(),
+    work = algorithmic_work(counts, len(wl.scene.regions))
+    achieved = work["flops_per_packet"] * args.packets / kernel_s / 1e12
+    atomics = work["atomics_per_packet"] * args.packets / kernel_s
+    f_alu = achieved / peak_tflops
+    f_atom = atomics / mb["atomics_distinct_per_s"]
+    alu = {"achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": f_alu,
+           "peak_basis": "measured: smcrt_microbench FP32 FMA kernel on this GPU "
+                         f"(nominal {sm_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz = {nominal_tflops:.1f} TFLOP/s)"}
+    atom = {"achieved": atomics, "peak": mb["atomics_distinct_per_s"], "unit": "int64 atomics/s", "frac": f_atom,
+            "peak_basis": "measured: smcrt_microbench int64 atomic adds to scattered addresses of a 64 MiB table",
+            "hot_32_address_rate": mb["atomics_hot_per_s"]}
+    top = alu if f_alu >= f_atom else atom
+    out["roofline"] = {"bound": "alu" if f_alu >= f_atom else "l2_atomics", "achieved": top["achieved"],
+                       "peak": top["peak"], "unit": top["unit"], "frac": max(f_alu, f_atom),
+                       "traffic": recorded_traffic(),
                        "traffic_note": "DRAM bytes per full-size launch from the ncu summary in profiles/ "
                                        "(null if the kernel changed since)",
-                       "peak_basis": "measured: smcrt_microbench FP32 FMA kernel on this GPU "
-                                     f"(nominal {sm_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz = "
-                                     f"{nominal_tflops:.1f} TFLOP/s)",
                        "kernel": f"packets_{args.precision}",
-                       "algorithmic_flops_per_packet": flops / args.packets,
-                       "atomics_per_s": atomics,
-                       "atomics_peak_distinct_per_s": mb["atomics_distinct_per_s"],
-                       "atomics_peak_hot_per_s": mb["atomics_hot_per_s"],
-                       "atomics_frac": atomics / mb["atomics_distinct_per_s"]}
+                       "frac_rule": "max(FP32 flops / FP32 peak, int64 atomics / atomic peak) over the "
+                                    "event-timed launch",
+                       "fp32": alu, "atomics": atom,
+                       "algorithmic_work": work,
+                       "work_basis": "FP64 oracle's event counters on a sample of the same workload and step "
+                                     "rule, times the per-event FP32 operation counts in bench.py"}
     # lane-issue view: executed thread instructions (ncu, per packet) against
     # the issue ceiling of 152 SMs x 4 schedulers x 32 lanes x clock
     tipp = recorded_traffic("thread_instructions_per_packet") if args.stepping == W.SEGMENT else None
@@ -512,58 +685,131 @@ def main():
     out["counters_per_packet"]["refined_fraction_of_fresnel"] = (
         totals_mixed["refined"] / max(1, totals_mixed["fresnel"]))
 
-    def timed_leg(wleg, precision, nsteps, tune):
+    if e2e_multi is not None:
+        out["e2e"] = e2e_multi
+
+    def leg_buffers(wleg):
+        gg = wleg.grid
+        return (torch.zeros((gg.n[2], gg.n[1], gg.n[0]), dtype=torch.int64, device="cuda"), smc.totals_tensor())
+
+    def timed_leg(wleg, precision, packets, nsteps, tune):
+        """Event-timed launches of ids [0, packets) after a warm-up, each
+        after an L2 flush; the autotuner picks the launch shape first."""
+        f, t = leg_buffers(wleg)
         p = ctx.plan(wleg, precision)
-        p.autotune(tune)
-        step(min(args.packets, 1_000_000), p, wleg.seed, id0)
+        choice = p.autotune(min(packets, tune))
+        f.zero_()
+        t.zero_()
+        p.launch(0, min(packets, 1_000_000), wleg.seed, f, t, None, stream.cuda_stream)
         torch.cuda.synchronize()
         evs = []
         for i in range(nsteps):
             l2_flush.fill_(float(i))
+            f.zero_()
+            t.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(args.packets, p, wleg.seed, id0)
+            p.launch(0, packets, wleg.seed, f, t, None, stream.cuda_stream)
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize()
+        assert p.status() == 0
         p.close()
-        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / nsteps, smc.totals_from_tensor(tot), flu.cpu().numpy()
+        sec = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / nsteps
+        return {"value": packets / sec, "unit": UNIT, "ms_per_step": 1e3 * sec, "packets": packets,
+                "steps": nsteps, "stepping": wleg.scene.stepping,
+                "launch": {"blocks": choice[0], "threads": choice[1], "variant": choice[2]}}, \
+            smc.totals_from_tensor(t)
 
-    if e2e_multi is not None:
-        out["e2e"] = e2e_multi
+    def batches(wleg, precision, packets, K, block):
+        """Ids [0, packets) as K launches of consecutive ids: per-batch R, T,
+        A and fluence block sums, all per packet (untimed)."""
+        f, t = leg_buffers(wleg)
+        fsum = torch.zeros_like(f)
+        p = ctx.plan(wleg, precision)
+        per = packets // K
+        rta, blocks = [], []
+        for k in range(K):
+            f.zero_()
+            t.zero_()
+            p.launch(k * per, per, wleg.seed, f, t, None, stream.cuda_stream)
+            fsum += f
+            blocks.append(block_sums(f, block) / FX / per)
+            tk = smc.totals_from_tensor(t)
+            rta.append([tk["R"] / FX / per, tk["T"] / FX / per, tk["A"] / FX / per, tk["max_steps_hit"]])
+        assert p.status() == 0
+        p.close()
+        return np.array(rta), np.array(blocks), fsum.cpu().numpy(), K * per
+
+    def equal_error(wleg, packets, K, block):
+        """Mixed against FP64 (bit-identical to the FP64 oracle per packet) on
+        the same K batches of ids: the paired R/T/A differences with their
+        sigma, and the fluence map block by block."""
+        rm, bm, fm, nb = batches(wleg, "mixed", packets, K, block)
+        rf, bf, ff, _ = batches(wleg, "fp64", packets, K, block)
+        nrm = float(np.linalg.norm(ff.astype(np.float64)))
+        d = {"packets": packets, "batches": K, "block_voxels": list(block),
+             "step_cap_kills": {"mixed": int(rm[:, 3].sum()), "fp64": int(rf[:, 3].sum())}}
+        for c, key in enumerate(("R", "T", "A")):
+            diff = rm[:, c] - rf[:, c]
+            sig = float(diff.std(ddof=1) / math.sqrt(K))
+            z = float(diff.mean() / sig) if sig > 0 else 0.0
+            d[key] = {"mixed": float(rm[:, c].mean()), "fp64": float(rf[:, c].mean()),
+                      "mixed_minus_fp64": float(diff.mean()), "sigma": sig, "z": z,
+                      "z_normal_equivalent": float(_z_from_t(z, K - 1)),
+                      "fp64_batch_sigma": float(rf[:, c].std(ddof=1) / math.sqrt(K))}
+        d["fluence_blocks"] = paired_block_stats(bm, bf)
+        d["fluence_rel_l2_mixed_vs_fp64"] = (float(np.linalg.norm((fm - ff).astype(np.float64))) / nrm
+                                             if nrm > 0 else None)
+        d["within_3_sigma"] = bool(all(abs(d[k]["z_normal_equivalent"]) < 3 for k in ("R", "T", "A"))
+                                   and d["fluence_blocks"].get("pass", False))
+        return d, (rm, bm, fm, nb), (rf, bf, ff, nb)
+
     if not args.quick and world == 1:
-        # ---- mixed precision with plain sphere tracing (the paper's step) ---
-        totals_st = None
+        # ---- the headline's comparison: plain FP64 with the SAME step rule,
+        # and both precisions with the paper's sphere tracing beside it ------
+        log("plain FP64 with the headline's step rule")
+        out["fp64"], _ = timed_leg(wl, "fp64", args.packets, args.fp64_steps, 200_000)
+        out["fp64"]["mixed_speedup"] = value / out["fp64"]["value"]
         if args.stepping != W.SPHERE_TRACING and args.precision == "mixed":
-            log(f"mixed {value:.3e} packets/s; timing mixed with sphere tracing")
-            t_st, totals_st, flu_legs["mixed_sphere_tracing"] = timed_leg(wl_plain, "mixed", 3,
-                                                                          min(args.packets, 2_000_000))
-            out["mixed_sphere_tracing"] = {"value": args.packets / t_st, "unit": UNIT, "ms_per_step": 1e3 * t_st,
-                                           "segment_speedup": t_st / kernel_s}
-        # ---- plain FP64 mode (sphere tracing) on the same workload ----------
-        log("timing the plain FP64 mode")
-        plan64 = ctx.plan(wl_plain, "fp64")
-        plan64.autotune(100_000)
-        step(min(args.packets, 1_000_000), plan64, wl.seed, id0)
-        torch.cuda.synchronize()
-        e64 = []
-        for i in range(args.fp64_steps):
-            l2_flush.fill_(float(i))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step(args.packets, plan64, wl.seed, id0)
-            b.record(stream)
-            e64.append((a, b))
-        torch.cuda.synchronize()
-        t64 = sum(a.elapsed_time(b) for a, b in e64) / 1e3 / args.fp64_steps
-        totals_fp64 = smc.totals_from_tensor(tot)
-        flu_legs["fp64"] = flu.cpu().numpy()
-        plan64.close()
-        out["fp64"] = {"value": args.packets / t64, "unit": UNIT, "ms_per_step": 1e3 * t64,
-                       "stepping": W.SPHERE_TRACING,
-                       "mixed_speedup": (args.packets / kernel_s) / (args.packets / t64)}
+            log("sphere tracing: mixed and FP64")
+            out["mixed_sphere_tracing"], totals_st = timed_leg(wl_plain, "mixed", args.packets, 3, 2_000_000)
+            out["mixed_sphere_tracing"]["segment_speedup"] = out["mixed_sphere_tracing"]["ms_per_step"] / (
+                1e3 * kernel_s)
+            out["fp64_sphere_tracing"], _ = timed_leg(wl_plain, "fp64", args.packets, 1, 200_000)
+            out["fp64_sphere_tracing"]["mixed_speedup"] = (out["mixed_sphere_tracing"]["value"]
+                                                           / out["fp64_sphere_tracing"]["value"])
+        out["mixed_vs_fp64"] = {
+            "same_step_rule": {args.stepping: value / out["fp64"]["value"]},
+            "note": "packets/s ratio with both precisions on one step rule; the segment-stepping gain is "
+                    "reported separately (mixed_sphere_tracing.segment_speedup)"}
+        if "fp64_sphere_tracing" in out:
+            out["mixed_vs_fp64"]["same_step_rule"][W.SPHERE_TRACING] = out["fp64_sphere_tracing"]["mixed_speedup"]
 
-        log(f"fp64 {args.packets / t64:.3e} packets/s; end-to-end leg")
+        # ---- equal error: mixed against FP64 on the same ids -----------------
+        log("equal error: paired mixed / FP64 batches")
+        ee, legm, legf = equal_error(wl, args.packets, 20, (10, 10, 10))
+        out["equal_error"] = ee
+        # each precision against the oracle sample (independent ids)
+        acc = {}
+        for name, (r, b, fmap, nmap) in (("mixed", legm), ("fp64", legf)):
+            dd = {}
+            for c, key in enumerate(("R", "T", "A")):
+                ov = osamp["records"][key] / FX
+                gv = r[:, c]
+                sig = math.sqrt(ov.var() / ov.size + gv.var(ddof=1) / gv.size)
+                dd[key] = float(gv.mean())
+                dd[f"{key}_oracle"] = float(ov.mean())
+                dd[f"{key}_z"] = float((gv.mean() - ov.mean()) / sig)
+            dd["fluence_blocks"] = block_stats(b, osamp["blocks"], paired=False)
+            dd.update(fluence_l2(fmap, nmap, osamp["halves"], osamp["half_packets"]))
+            acc[name] = dd
+        acc["note"] = ("GPU at 1e7 packets in 20 batches against an independent oracle sample in 10 batches; "
+                       "z = difference / combined MC sigma; fluence compared block by block (Welch), and as "
+                       "the relative L2 difference per packet beside the oracle sample's half-sample noise")
+        out["accuracy_vs_oracle"] = acc
+
+        log("end-to-end leg")
         # ---- end to end through the public API with host buffers -------------
         m = smc.Marshalled(wl.scene, wl.source, wl.grid)
         h_flu = np.zeros((g.n[2], g.n[1], g.n[0]), dtype=np.int64)
@@ -581,38 +827,32 @@ def main():
                       "d2h_bytes_per_step": int(h_flu.nbytes + C.sizeof(smc.Totals)),
                       "api": "smcrt_run with host scene structs and a host fluence buffer"}
 
-        log("oracle leg")
-        # ---- accuracy against the FP64 oracle, and the oracle's CPU timing ----
-        o_pps, o_n, o_threads, o_rec, o_halves = oracle_sample(wl, args.oracle_seconds, id_base=0)
-        out["cpu_baseline"] = {"value": o_pps, "unit": UNIT, "cores": o_threads, "kind": "oracle",
-                               "sample": f"{o_n} packets (ids 0..{o_n - 1}) of the same three_layer_slab "
-                                         f"workload ({args.stepping} stepping), FP64, {o_threads} threads"}
-        acc = {}
-        legs = [("mixed", totals_mixed), ("fp64", totals_fp64)]
-        if totals_st is not None:
-            legs.append(("mixed_sphere_tracing", totals_st))
-        for name, t in legs:
-            d = {}
-            for k in ("R", "T", "A"):
-                ov = o_rec[k] / FX
-                sig = math.sqrt(ov.var() / ov.size + ov.var() / args.packets)
-                gv = t[k] / FX / args.packets
-                d[k] = gv
-                d[f"{k}_oracle"] = float(ov.mean())
-                d[f"{k}_z"] = (gv - float(ov.mean())) / sig
-            d.update(fluence_l2(flu_legs[name], args.packets, o_halves, o_n // 2))
-            acc[name] = d
-        out["accuracy_vs_oracle"] = acc
-        out["accuracy_vs_oracle"]["note"] = ("GPU at 1e7 packets vs oracle sample; z = difference / combined "
-                                             "MC sigma; fluence_rel_l2 = |phi_gpu - phi_oracle| / |phi_oracle| "
-                                             "per packet, beside the oracle sample's own noise. FP64 mode is "
-                                             "bit-identical to the oracle packet by packet")
+        # ---- the other configs: packets/s of both precisions, equal error ---
+        if not args.no_configs:
+            log("configs 0, 2, 3")
+            cfgs = {}
+            runs = [("config0_sphere_pencil", W.sphere_pencil(), 100_000, 100_000, 5, 1_000_000, (5, 5, 5)),
+                    ("config2_vessel_network", W.vessel_network(), 100_000_000, args.cfg_fp64_packets,
+                     args.cfg_steps, args.cfg_fp64_packets, (20, 20, 20)),
+                    ("config3_glass_container", W.glass_container(), 100_000_000, args.cfg_fp64_packets,
+                     args.cfg_steps, args.cfg_fp64_packets, (16, 16, 16))]
+            for name, wc, n_mixed, n_fp64, nst, n_acc, blk in runs:
+                wc = wc.with_stepping(args.stepping)
+                log(f"  {name}")
+                e = {"workload": wc.name, "grid": list(wc.grid.n), "stepping": args.stepping}
+                e["mixed"], tmc = timed_leg(wc, "mixed", n_mixed, nst, 2_000_000)
+                e["mixed"]["max_steps_hit"] = tmc["max_steps_hit"]
+                e["fp64"], _ = timed_leg(wc, "fp64", n_fp64, 1 if n_fp64 > 200_000 else 3, 20_000)
+                e["mixed_over_fp64"] = e["mixed"]["value"] / e["fp64"]["value"]
+                e["equal_error"], _, _ = equal_error(wc, n_acc, 20, blk)
+                cfgs[name] = e
+            out["configs"] = cfgs
 
         if not args.no_paper_cases and args.precision == "mixed":
             log("paper cases (Table 2 sizes)")
             out["paper_cases"] = paper_cases(ctx, smc, stream, args.stepping)
 
-        # ---- served mix: Poisson arrivals at 80% of measured capacity ---------
+        # ---- served mix (config 4): Poisson arrivals at 80% of capacity -------
         if args.serve_jobs > 0:
             log("serving leg")
             # capacity of the server on this mix: all jobs of a prefix at once

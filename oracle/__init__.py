@@ -72,7 +72,9 @@ class OrGrid(C.Structure):
 
 
 TOTAL_FIELDS = ["R", "T", "A", "killed", "gain", "packets", "scatters", "steps", "scene_evals",
-                "prog_evals", "prim_evals", "interfaces", "fresnel", "pieces", "max_steps_hit"]
+                "prog_evals", "prim_evals", "interfaces", "fresnel", "pieces", "max_steps_hit",
+                "prim_sphere", "prim_box", "prim_capsule", "prim_torus", "prim_cylinder", "smooth_ops",
+                "seg_calls", "seg_sphere", "seg_box", "seg_capsule", "seg_torus", "seg_cylinder", "seg_moves"]
 
 
 class OrTotals(C.Structure):

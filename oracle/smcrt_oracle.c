@@ -76,6 +76,12 @@ typedef struct {
     int64_t R, T, A, killed, gain;       /* fixed point, 2^-32 weight units */
     int64_t packets, scatters, steps, scene_evals, prog_evals, prim_evals;
     int64_t interfaces, fresnel, pieces, max_steps_hit;
+    /* work counters (no effect on the transport): primitive SDF evaluations
+     * by kind (sphere, box, capsule, torus, cylinder), smooth-union
+     * operations, segment-stepping bound calls and the primitive ray bounds
+     * taken in them by kind */
+    int64_t prim_kind[5], smooth_ops, seg_calls, seg_kind[5];
+    int64_t seg_moves;    /* segment-stepping moves that did not end in an interaction */
 } or_totals;
 typedef struct { int64_t R, T, A, killed, gain, scatters, steps, pad; } or_packet;
 
@@ -314,11 +320,12 @@ static double region_sdf(const or_scene *S, int r, const double p[3], or_totals 
         const or_node *nd = &S->nodes[R->begin + i];
         if (nd->op == 0) {
             st[sp++] = sdf_prim(S, &S->prims[nd->prim], p);
-            if (T) T->prim_evals += 1;
+            if (T) { T->prim_evals += 1; T->prim_kind[S->prims[nd->prim].kind] += 1; }
         } else {
             double b = st[--sp];
             double a = st[--sp];
             st[sp++] = csg_apply(nd->op, a, b, nd->k);
+            if (T && nd->op == 2) T->smooth_ops += 1;
         }
     }
     return st[0];
@@ -820,16 +827,21 @@ static double segment_prim(const or_scene *S, const or_prim *pr, const double p[
 }
 
 /* Largest safe move from p along u (scene evaluated at p in E). */
-static double segment_bound(const or_scene *S, const or_eval *E, const double p[3], const double u[3])
+static double segment_bound(const or_scene *S, const or_eval *E, const double p[3], const double u[3],
+                            or_totals *T)
 {
     double dh = 0.5 * S->delta;
     double t = E->dsoft - dh;
+    if (T) T->seg_calls += 1;
     for (int r = 0; r < S->nregions; ++r) {
         if (region_soft(S, r)) continue;
         const or_region *R = &S->regions[r];
         for (int i = 0; i < R->count; ++i) {
             const or_node *nd = &S->nodes[R->begin + i];
-            if (nd->op == 0) t = fmin(t, segment_prim(S, &S->prims[nd->prim], p, u, dh));
+            if (nd->op == 0) {
+                t = fmin(t, segment_prim(S, &S->prims[nd->prim], p, u, dh));
+                if (T) T->seg_kind[S->prims[nd->prim].kind] += 1;
+            }
         }
     }
     double c[3], h[3];
@@ -857,6 +869,7 @@ static void run_packet(const or_scene *S, const or_source *src, const or_grid *G
         or_eval E = scene_eval(S, p, T);
         if (E.dbox > 0.0) goto escape;         /* outside the volume of interest */
         double L;
+        int traced = 0;                        /* counting only: a tracing move */
         if (E.dmin < S->delta) {
             int r = interface_step(S, &E, p, u, &rng, T);
             if (r == 2) goto escape;
@@ -864,7 +877,8 @@ static void run_packet(const or_scene *S, const or_source *src, const or_grid *G
             L = S->delta;                      /* not approaching: forced step */
         } else {
             L = E.dmin - 0.5 * S->delta;       /* stop short: never cross by rounding */
-            if (S->stepping == 1) L = fmax(L, segment_bound(S, &E, p, u));
+            traced = 1;
+            if (S->stepping == 1) L = fmax(L, segment_bound(S, &E, p, u, T));
         }
         {
             double mu_a = 0.0, mu_s = 0.0, g = 0.0;
@@ -899,6 +913,7 @@ static void run_packet(const or_scene *S, const or_source *src, const or_grid *G
                 tau = -or_log(xi[3]);
             } else {
                 or_tally(G, p, u, L, w, flu, &T->pieces);
+                if (traced && S->stepping == 1) T->seg_moves += 1;
                 tau = tau - mu_t * L;
                 p[0] = p[0] + L * u[0]; p[1] = p[1] + L * u[1]; p[2] = p[2] + L * u[2];
             }
@@ -975,7 +990,7 @@ double or_segment_step(const or_scene *S, const double p[3], const double u[3])
 {
     or_eval E = scene_eval(S, p, NULL);
     if (!(E.dmin >= S->delta)) return 0.0;
-    return fmax(E.dmin - 0.5 * S->delta, segment_bound(S, &E, p, u));
+    return fmax(E.dmin - 0.5 * S->delta, segment_bound(S, &E, p, u, NULL));
 }
 
 double or_region_sdf(const or_scene *S, int r, const double p[3])

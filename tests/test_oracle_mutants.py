@@ -51,8 +51,8 @@ MUTANTS = [
     ("segment_box_margin", "double e = d > 0.0 ? dh : -dh;", "double e = d > 0.0 ? 0.0 : -dh;"),
     ("segment_sphere_root", "t = cc / (sqrt(disc) - b);", "t = sqrt(disc) - b;"),
     ("segment_soft_bound", "if (region_soft(S, r) && ad < E.dsoft) E.dsoft = ad;", "if (0 && ad < E.dsoft) E.dsoft = ad;"),
-    ("segment_step_rule", "if (S->stepping == 1) L = fmax(L, segment_bound(S, &E, p, u));",
-     "if (S->stepping == 1) L = fmin(L, segment_bound(S, &E, p, u));"),
+    ("segment_step_rule", "if (S->stepping == 1) L = fmax(L, segment_bound(S, &E, p, u, T));",
+     "if (S->stepping == 1) L = fmin(L, segment_bound(S, &E, p, u, T));"),
     ("torus_tube_radius", "return sqrt(ring * ring + dz * dz) - q[4];", "return sqrt(ring * ring + dz * dz) - q[3];"),
     ("cylinder_cap", "double b = fabs(dz) - q[4];", "double b = dz - q[4];"),
     ("frame_rotation_transposed", "double q[3];\n    q[0] = (X->rot[0] * vx + X->rot[3] * vy + X->rot[6] * vz) / X->s;",
