@@ -3,7 +3,12 @@
 Translation units and their floating-point flags:
   smcrt_k64.cu   FP64 packet kernel, -fmad=false (no FMA contraction, so the
                  kernel's arithmetic is the reference's IEEE sequence);
-  smcrt_k32.cu   mixed kernel, approximate FP32 division/sqrt, FTZ;
+  smcrt_k32.cu   mixed kernel, approximate FP32 division/sqrt, FTZ; the
+                 multiply-adds are fused where the front end writes them
+                 (explicit FMAs in the PTX) and nowhere else: the assembler
+                 may not fuse plain multiply / add pairs (--fmad=false),
+                 because it fused them differently under different register
+                 budgets, and every instantiation must give the same bits;
   smcrt_util.cu  helper kernels;
   smcrt_api.cpp  host runtime (C-ABI), -ffp-contract=off.
 """
@@ -28,7 +33,7 @@ COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
 
 UNITS = {
     "smcrt_k64.cu": ["-fmad=false"],
-    "smcrt_k32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "smcrt_k32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-Xptxas", "--fmad=false"],
     "smcrt_util.cu": [],
     "smcrt_noalloc.cu": [],
     "smcrt_microbench.cu": [],

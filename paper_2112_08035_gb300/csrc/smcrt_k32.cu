@@ -28,8 +28,7 @@ constexpr float kLandCos = 0.25f;     // line-preserving landing down to this |c
 // of a glass shell drifts into total internal reflection at both walls and
 // stays there.  Directions within kLandCos of the plane move a / kLandCos
 // along v and the rest of the distance along n, so no landing moves more than
-// 4 a.  Like a push along n, the landing puts the packet a deeper without
-// drawing an interaction over the way there.
+// 4 a.  The path of the landing is charged afterwards (cross32).
 __device__ __forceinline__ void land32(float qx, float qy, float qz, float vx, float vy, float vz, float nx,
                                        float ny, float nz, float a, float sd, float &px, float &py, float &pz)
 {
@@ -39,6 +38,36 @@ __device__ __forceinline__ void land32(float qx, float qy, float qz, float vx, f
     px = qx + s * vx + rest * nx;
     py = qy + s * vy + rest * ny;
     pz = qz + s * vz + rest * nz;
+}
+
+// The interface shortcut in FP32.  A packet reaches a surface when it is
+// within delta32 of it, is placed on the surface point q and lands about
+// 2 delta32 beyond it; the FP64 reference makes the same moves at its delta
+// (30 times smaller for the layered slab), where the path skipped is
+// negligible.  At delta32 it is not: the approach from the arrival point p to
+// the surface (|d| / |cos| along the ray, |cos| floored like the landing's)
+// and the landing q -> P would pass through medium without attenuation or
+// fluence, which measurably raised the slab's transmission (by 0.15 % of T
+// at 1e7 packets, paired against the FP64 kernel; the bias grows linearly
+// with the threshold in the oracle).  So the mixed kernel treats that path
+// as travelled: when the optical depth left runs out on the approach, the
+// packet interacts on the near side (at its arrival point) instead of
+// crossing; otherwise the crossing (cross32) charges the optical depth of
+// both pieces, each with its own region's mu_t (the packet interacts at once
+// if the landing exhausts it), and their length is tallied with the next
+// move: its segment is extended back from the landing point by that length
+// (the pieces are a few delta32 long, far below a voxel, and reach at most
+// one voxel boundary beyond the surface).  Depositing them separately added
+// atomics to the voxel where a pencil beam enters, which every packet's
+// first tally piece already hits, and serialised there (10 % of the slab's
+// time).
+// Length of the approach from a point |dstar| from the surface along a ray
+// with |u.n| = |cdot| (floored at kLandCos, as the landing is).  Explicitly
+// rounded operations here and in cross32's charge: no multiply-add is
+// contracted, so every register-budget instantiation computes the same bits.
+__device__ __forceinline__ float approach_len32(float dstar, float cdot)
+{
+    return __fdividef(fabsf(dstar), fmaxf(fabsf(cdot), kLandCos));
 }
 
 __device__ __forceinline__ float hg_cos32(float g, float xi)
@@ -153,6 +182,123 @@ __device__ __noinline__ void refine64(const DevScene &S, int istar, int rnear, i
     pz = (float)(qz + s * vz + rest * nz);
 }
 
+// A crossing of a surface (Sec. 2.3), out of line: Fresnel reflection or
+// Snell refraction when the refractive index changes (FP32 on planar faces,
+// refine64 where the cosines are ill-conditioned or the normal is noisy),
+// or a straight crossing when it does not (matched); the line-preserving
+// landing; and the charge of the interface shortcut: the optical depth of
+// the approach (arrival point a to the surface) and of the landing (surface
+// point q to the landing point P), each with its own region's mu_t; their
+// length is returned for the next move's tally.  The new state is returned
+// by value, so the loop's own variables stay in registers.
+struct Crossed {
+    float px, py, pz, ux, uy, uz, tau;
+    float pend;      // the shortcut's length, tallied with the next move
+    int refined;
+};
+
+template <bool G>
+static __device__ __noinline__ Crossed cross32(const DevScene &S, float ux, float uy, float uz, float qx, float qy,
+                                               float qz, float nx, float ny, float nz, float tau, float dstar,
+                                               float cdot, int istar, int rnear, int rfar, uint32_t xiw, bool matched)
+{
+    const float sg = cdot > 0.f ? 1.f : -1.f;
+    const float a = 2.f * S.delta32;
+    Crossed o;
+    o.refined = 0;
+    o.ux = ux; o.uy = uy; o.uz = uz;
+    if (matched) {                                  // same index: cross on the ray
+        land32(qx, qy, qz, ux, uy, uz, nx, ny, nz, a, sg, o.px, o.py, o.pz);
+    } else {
+        const float n1 = region_n32(S, rnear), n2 = region_n32(S, rfar);
+        const float ci = fabsf(cdot);
+        const float eta = n1 / n2;
+        const float st2 = eta * eta * ((1.f - ci) * (1.f + ci));
+        const int zeros = (nx == 0.f) + (ny == 0.f) + (nz == 0.f);
+        const bool curved_noisy = !S.analytic_nrm && zeros != 2;   // probe normals on curved faces
+        if (ci < kGrazeCos || fabsf(st2 - 1.f) < kCritBand || curved_noisy) {
+            o.refined = 1;
+            o.px = qx; o.py = qy; o.pz = qz;
+            refine64<G>(S, istar, rnear, rfar, sg, xiw, o.px, o.py, o.pz, o.ux, o.uy, o.uz, nx, ny, nz);
+        } else {                                    // planar face: the FP32 normal is exact
+            float R = 1.f, ct = 0.f;
+            if (st2 < 1.f) {
+                ct = sqrtf(1.f - st2);
+                const float rs = __fdividef(n1 * ci - n2 * ct, n1 * ci + n2 * ct);
+                const float rp = __fdividef(n1 * ct - n2 * ci, n1 * ct + n2 * ci);
+                R = 0.5f * (rs * rs + rp * rp);
+            }
+            float sd;
+            if (u01_32(xiw) <= R) {
+                const float c2 = 2.f * cdot;
+                o.ux -= c2 * nx; o.uy -= c2 * ny; o.uz -= c2 * nz;
+                sd = -sg;
+            } else {
+                const float k = sg * (eta * ci - ct);
+                o.ux = eta * o.ux - k * nx; o.uy = eta * o.uy - k * ny; o.uz = eta * o.uz - k * nz;
+                sd = sg;
+            }
+            normalise32(o.ux, o.uy, o.uz);
+            land32(qx, qy, qz, o.ux, o.uy, o.uz, nx, ny, nz, a, sd, o.px, o.py, o.pz);
+        }
+    }
+    // the side the packet landed on: beyond the surface (refracted, matched)
+    // or back on the near side (reflected, or tangent in FP64)
+    const bool far = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(o.px, qx), nx),
+                                                   __fmul_rn(__fsub_rn(o.py, qy), ny)),
+                                         __fmul_rn(__fsub_rn(o.pz, qz), nz)),
+                               sg) > 0.f;
+    const int rside = far ? rfar : rnear;
+    // the shortcut's charge (explicitly rounded: no contraction)
+    const float lnear = approach_len32(dstar, cdot);
+    const float dx = __fsub_rn(o.px, qx), dy = __fsub_rn(o.py, qy), dz = __fsub_rn(o.pz, qz);
+    const float lfar = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+    const float mn = rnear >= 0 ? (*(S.reg32 + 2 * rnear)).x : 0.f;
+    const float mf = rside >= 0 ? (*(S.reg32 + 2 * rside)).x : 0.f;
+    o.tau = fmaxf(__fsub_rn(__fsub_rn(tau, __fmul_rn(mn, lnear)), __fmul_rn(mf, lfar)), 0.f);
+    o.pend = __fadd_rn(lnear, lfar);
+    return o;
+}
+
+// Photon release (Sec. 2.1), out of line: position and direction from the
+// source (pencil, disc, square, isotropic point) and the first optical depth
+// (Eq. 1), from one Philox call's words.
+struct Launched {
+    float px, py, pz, ux, uy, uz, tau;
+};
+
+static __device__ __noinline__ Launched launch32(const DevScene &S, uint4 r)
+{
+    Launched o;
+    const float x0 = u01_32(r.x), x1 = u01_32(r.y);
+    o.px = S.src_pos32[0]; o.py = S.src_pos32[1]; o.pz = S.src_pos32[2];
+    o.ux = S.src_dir32[0]; o.uy = S.src_dir32[1]; o.uz = S.src_dir32[2];
+    if (S.src_kind == 1 || S.src_kind == 2) {
+        float c1, c2;
+        if (S.src_kind == 1) {
+            const float rho = S.src_radius32 * sqrtf(x0);
+            float sn, cs;
+            __sincosf(6.2831853f * x1, &sn, &cs);
+            c1 = rho * cs;
+            c2 = rho * sn;
+        } else {
+            c1 = S.src_radius32 * (2.f * x0 - 1.f);
+            c2 = S.src_radius32 * (2.f * x1 - 1.f);
+        }
+        o.px += c1 * S.src_b132[0] + c2 * S.src_b232[0];
+        o.py += c1 * S.src_b132[1] + c2 * S.src_b232[1];
+        o.pz += c1 * S.src_b132[2] + c2 * S.src_b232[2];
+    } else if (S.src_kind == 3) {
+        const float ct = 2.f * x0 - 1.f;
+        const float st = sqrtf(fmaxf((1.f - ct) * (1.f + ct), 0.f));
+        float sn, cs;
+        __sincosf(6.2831853f * x1, &sn, &cs);
+        o.ux = st * cs; o.uy = st * sn; o.uz = ct;
+    }
+    o.tau = -__logf(u01_32(r.w));
+    return o;
+}
+
 // Per-warp shared state: the staged scene and the warp's tally slots.
 // Scene-table staging (a launch option the autotuner tries): the warp copies
 // the instruction stream, primitive kinds, FP32 primitive and region tables
@@ -222,6 +368,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
     // an anchor q and its length cs along u, and places the packet at
     // q + cs u (one rounding, whatever the step count).  cs < 0: no crawl.
     float cs = -1.f;
+    float pend = 0.f;                    // track length of a crossing's shortcut, tallied with the next move
     float nx = 0, ny = 0, nz = 0, cdot = 0, fplus = 0, dstar = 0;
     int phase = kTrace, sub = 0, istar = -1, reg = -1, rfar = -1;
     int nsteps = 0;
@@ -236,7 +383,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
-            if (need && dfr != nullptr) {
+            if (SMCRT_RARE(need && dfr != nullptr)) {
                 const int leader = __ffs(need) - 1;
                 unsigned base = 0u, avail = 0u;
                 if (lane == leader) {
@@ -259,6 +406,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                         nsteps = (int)d.nsteps; pscat = d.pscat;
                         phase = kTrace;
                         cs = __uint_as_float(d.pad[0]);
+                        pend = __uint_as_float(d.pad[1]);
                         if (cs >= 0.f) {           // parked in a crawl: p holds the anchor
                             qx = px; qy = py; qz = pz;
                             px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
@@ -299,12 +447,12 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         const float sg = cdot > 0.f ? 1.f : -1.f;
         float ex = px, ey = py, ez = pz;
         int sel = -2;
-        if (phase == kNrm) {
+        if (SMCRT_RARE(phase == kNrm)) {
             const float hh = (sub & 1) ? -hstep : hstep;
             const int a = sub >> 1;
             if (a == 0) ex = px + hh; else if (a == 1) ey = py + hh; else ez = pz + hh;
             sel = istar;
-        } else if (phase == kFar || phase == kNear) {
+        } else if (SMCRT_RARE(phase == kFar || phase == kNear)) {
             const float e = (phase == kFar ? 2.f : -2.f) * delta * sg;
             ex = qx + e * nx; ey = qy + e * ny; ez = qz + e * nz;
         }
@@ -319,12 +467,14 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         bool seg_step = false;                 // a tracing move that segment stepping may lengthen
         bool crawl = false;                    // a forced step away from a surface
         bool fin = false;                      // the packet ends this iteration
+        bool near_hit = false;                 // interacts before reaching the surface
+        bool matched = false;                  // a crossing without an index change
         long long fin_R = 0, fin_T = 0, fin_K = 0;
         float L = 0.f;
         int rnear = -1;
         if (alive) {
             if (phase == kTrace) {
-                if (E.dbox > 0.f) {
+                if (SMCRT_RARE(E.dbox > 0.f)) {
                     {                                          // leaves the volume: R or T
                         const long long v = fx32(w);
                         if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
@@ -333,7 +483,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                     }
                 } else {
                     reg = E.region;
-                    if (E.dmin < delta) {
+                    if (SMCRT_RARE(E.dmin < delta)) {
                         istar = E.istar;
                         dstar = E.dstar;
                         if (S.analytic_nrm) {              // gradient of a short program, now
@@ -349,7 +499,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                         seg_step = S.stepping == SMCRT_STEP_SEGMENT;
                     }
                 }
-            } else if (phase == kNrm) {
+            } else if (SMCRT_RARE(phase == kNrm)) {
                 const float f = E.dsel;
                 if ((sub & 1) == 0) {
                     fplus = f;
@@ -358,29 +508,24 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                     const int a = sub >> 1;
                     if (a == 0) nx = gg; else if (a == 1) ny = gg; else nz = gg;
                 }
-                if (++sub == 6) nrm_ready = true;
+                if (++sub >= 6) nrm_ready = true;
             } else if (phase == kFar) {
                 rfar = E.region;
                 phase = kNear;
             } else if (phase == kNear) {
                 rnear = E.region;
-                if (region_n32(S, rnear) == region_n32(S, rfar)) {
-                    // matched indices: cross on the ray, as a Fresnel landing
-                    // does.  A push along n alone never advances along u, and
-                    // where the normal turns between the two sides (a smooth
-                    // union's crease) a packet moving along the wall was
-                    // pushed back and forth across it until the step cap.
-                    land32(qx, qy, qz, ux, uy, uz, nx, ny, nz, 2.f * delta, sg, px, py, pz);
-                    phase = kTrace;
-                    iter_done = true;
-                } else {
-                    fresnel = true;
-                }
+                // matched indices cross on the ray, as a Fresnel landing does
+                // (cross32).  A push along n alone never advances along u, and
+                // where the normal turns between the two sides (a smooth
+                // union's crease) a packet moving along the wall was pushed
+                // back and forth across it until the step cap.
+                matched = region_n32(S, rnear) == region_n32(S, rfar);
+                fresnel = true;
             }
         }
 
         // ---- 3b. a normal is ready (analytic, or after the sixth probe)
-        if (nrm_ready) {
+        if (SMCRT_RARE(nrm_ready)) {
             const float l2 = nx * nx + ny * ny + nz * nz;
             bool approaching = false;
             if (l2 > 0.f) {
@@ -398,6 +543,13 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 if (ux * S.src_dir32[0] + uy * S.src_dir32[1] + uz * S.src_dir32[2] < 0.f) fin_R = v; else fin_T = v;
                 fin = true;
                 alive = false;
+            } else if (tau < __fmul_rn(reg >= 0 ? (*(S.reg32 + 2 * reg)).x : 0.f, approach_len32(dstar, cdot))) {
+                // the optical depth runs out before the surface: interact here,
+                // at the arrival point (inside this region by evaluation).  Moving
+                // on by tau / mu_t could round the point across the surface, and
+                // a packet scattered just inside a clear glass wall can take a
+                // direction that total internal reflection traps at both walls.
+                near_hit = true;
             } else {
                 wadd(wa, kIntf, 1);
                 qx = px - dstar * nx; qy = py - dstar * ny; qz = pz - dstar * nz;
@@ -407,7 +559,12 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         }
 
         // ---- 4. move: interaction point or sphere-trace step, one tally site
-        bool interact = false;
+        bool interact = near_hit;
+        if (SMCRT_RARE(near_hit)) {
+            cs = -1.f;
+            phase = kTrace;                        // also after the sixth probe
+            iter_done = true;
+        }
         if (move) {
             float mu_t = 0.f, imu_t = 0.f;
             if (reg >= 0) {
@@ -415,14 +572,17 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 mu_t = RG.x; imu_t = RG.y;
             }
             interact = mu_t > 0.f && tau < mu_t * L;
-            if (seg_step && !interact) {           // segment stepping: a longer move along u
+            if (SMCRT_RARE(seg_step && !interact)) {           // segment stepping: a longer move along u
                 L = fmaxf(L, segment_bound32<G>(S, E.dsoft, E.dbox, px, py, pz, ux, uy, uz));
                 interact = mu_t > 0.f && tau < mu_t * L;
             }
             const float seg = interact ? tau * imu_t : L;
             long long *const flu = (long long *)jc->flu;
-            if (flu) tally32(S, flu, px, py, pz, ux, uy, uz, seg, w, &npieces);
-            if (crawl) {
+            // the segment starts back at the surface after a crossing (pend)
+            if (flu) tally32(S, flu, px - pend * ux, py - pend * uy, pz - pend * uz, ux, uy, uz, seg + pend, w,
+                             &npieces);
+            pend = 0.f;
+            if (SMCRT_RARE(crawl)) {
                 if (cs < 0.f) { qx = px; qy = py; qz = pz; cs = 0.f; }
                 cs += seg;
                 px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
@@ -436,7 +596,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         }
 
         // ---- 5. one Philox call for every lane that draws this iteration
-        const bool draws = alive && (phase == kLaunch || interact || fresnel);
+        const bool draws = alive && (phase == kLaunch || interact || (fresnel && !matched));
         uint4 r = make_uint4(0u, 0u, 0u, 0u);
         if (__any_sync(SMCRT_FULL, draws)) {
             r = philox4x32_10(make_uint4(event, 0u, id_lo, id_hi), jc->k0, jc->k1);
@@ -444,36 +604,15 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         }
 
         // ---- 6. consumers
-        if (alive && phase == kLaunch) {           // photon release (Sec. 2.1)
-            const float x0 = u01_32(r.x), x1 = u01_32(r.y);
-            px = S.src_pos32[0]; py = S.src_pos32[1]; pz = S.src_pos32[2];
-            ux = S.src_dir32[0]; uy = S.src_dir32[1]; uz = S.src_dir32[2];
-            if (S.src_kind == 1 || S.src_kind == 2) {
-                float c1, c2;
-                if (S.src_kind == 1) {
-                    const float rho = S.src_radius32 * sqrtf(x0);
-                    float sn, cs;
-                    __sincosf(6.2831853f * x1, &sn, &cs);
-                    c1 = rho * cs;
-                    c2 = rho * sn;
-                } else {
-                    c1 = S.src_radius32 * (2.f * x0 - 1.f);
-                    c2 = S.src_radius32 * (2.f * x1 - 1.f);
-                }
-                px += c1 * S.src_b132[0] + c2 * S.src_b232[0];
-                py += c1 * S.src_b132[1] + c2 * S.src_b232[1];
-                pz += c1 * S.src_b132[2] + c2 * S.src_b232[2];
-            } else if (S.src_kind == 3) {
-                const float ct = 2.f * x0 - 1.f;
-                const float st = sqrtf(fmaxf((1.f - ct) * (1.f + ct), 0.f));
-                float sn, cs;
-                __sincosf(6.2831853f * x1, &sn, &cs);
-                ux = st * cs; uy = st * sn; uz = ct;
-            }
-            tau = -__logf(u01_32(r.w));
+        if (SMCRT_RARE(alive && phase == kLaunch)) {           // photon release (Sec. 2.1)
+            const Launched L0 = launch32(S, r);
+            px = L0.px; py = L0.py; pz = L0.pz;
+            ux = L0.ux; uy = L0.uy; uz = L0.uz;
+            tau = L0.tau;
             w = 1.f;
             nsteps = 0; pA = 0; pG = 0; pscat = 0;
             cs = -1.f;
+            pend = 0.f;
             phase = kTrace;
         }
         if (interact) {                            // implicit capture, HG, roulette
@@ -485,7 +624,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             pscat += 1u;
             cs = -1.f;
             tau = -__logf(u01_32(r.w));
-            if (w < (float)kWRoulette) {
+            if (SMCRT_RARE(w < (float)kWRoulette)) {
                 if (u01_32(r.z) <= (float)(1.0 / kRouletteM)) {
                     pG += fx32(w * (float)(kRouletteM - 1.0));
                     w = w * (float)kRouletteM;
@@ -496,45 +635,21 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 }
             }
         }
-        if (fresnel) {                             // reflect or refract (Sec. 2.3)
-            wadd(wa, kFres, 1);
-            const float n1 = region_n32(S, rnear), n2 = region_n32(S, rfar);
-            const float ci = fabsf(cdot);
-            const float eta = n1 / n2;
-            const float st2 = eta * eta * ((1.f - ci) * (1.f + ci));
-            const int zeros = (nx == 0.f) + (ny == 0.f) + (nz == 0.f);
-            const bool curved_noisy = !S.analytic_nrm && zeros != 2;   // probe normals on curved faces
-            if (ci < kGrazeCos || fabsf(st2 - 1.f) < kCritBand || curved_noisy) {
-                wadd(wa, kRefined, 1);
-                refine64<G>(S, istar, rnear, rfar, sg, r.x, qx, qy, qz, ux, uy, uz, nx, ny, nz);
-                px = qx; py = qy; pz = qz;
-            } else {                               // planar face: the FP32 normal is exact
-                float R = 1.f, ct = 0.f;
-                if (st2 < 1.f) {
-                    ct = sqrtf(1.f - st2);
-                    const float rs = __fdividef(n1 * ci - n2 * ct, n1 * ci + n2 * ct);
-                    const float rp = __fdividef(n1 * ct - n2 * ci, n1 * ct + n2 * ci);
-                    R = 0.5f * (rs * rs + rp * rp);
-                }
-                float sd;
-                if (u01_32(r.x) <= R) {
-                    const float c2 = 2.f * cdot;
-                    ux -= c2 * nx; uy -= c2 * ny; uz -= c2 * nz;
-                    sd = -sg;
-                } else {
-                    const float k = sg * (eta * ci - ct);
-                    ux = eta * ux - k * nx; uy = eta * uy - k * ny; uz = eta * uz - k * nz;
-                    sd = sg;
-                }
-                normalise32(ux, uy, uz);
-                land32(qx, qy, qz, ux, uy, uz, nx, ny, nz, 2.f * delta, sd, px, py, pz);
-            }
+        if (SMCRT_RARE(fresnel)) {                             // reflect, refract or cross (Sec. 2.3)
+            const Crossed c = cross32<G>(S, ux, uy, uz, qx, qy, qz, nx, ny, nz, tau, dstar, cdot, istar, rnear, rfar,
+                                         r.x, matched);
+            if (!matched) wadd(wa, kFres, 1);
+            if (c.refined) wadd(wa, kRefined, 1);
+            px = c.px; py = c.py; pz = c.pz;
+            ux = c.ux; uy = c.uy; uz = c.uz;
+            tau = c.tau;
+            pend = c.pend;
             phase = kTrace;
             iter_done = true;
         }
         if (iter_done && alive) {
             nsteps += 1;
-            if (nsteps >= S.max_steps) {
+            if (SMCRT_RARE(nsteps >= S.max_steps)) {
                 wadd(wa, kCap, 1);
                 fin_K = fx32(w);
                 fin = true;
@@ -542,7 +657,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             }
         }
         // ---- a terminated packet: one bookkeeping site per iteration
-        if (fin) {
+        if (SMCRT_RARE(fin)) {
             wadd(wa, kR, fin_R); wadd(wa, kT, fin_T); wadd(wa, kKilled, fin_K);
             wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
             wadd(wa, kPackets, 1);
@@ -558,7 +673,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         // ---- park a straggler at a trace boundary (serving rounds only).  A
         // packet in a crawl is parked as its anchor and crawl length, from
         // which the resume recomputes the same position.
-        if (alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget) {
+        if (SMCRT_RARE(alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget)) {
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
             const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);
@@ -567,6 +682,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 const bool in_crawl = cs >= 0.f;
                 d.p[0] = in_crawl ? qx : px; d.p[1] = in_crawl ? qy : py; d.p[2] = in_crawl ? qz : pz;
                 d.pad[0] = __float_as_uint(cs);
+                d.pad[1] = __float_as_uint(pend);
                 d.u[0] = ux; d.u[1] = uy; d.u[2] = uz;
                 d.w = w; d.tau = tau;
                 d.pA = pA; d.pG = pG;

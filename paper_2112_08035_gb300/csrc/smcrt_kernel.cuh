@@ -36,6 +36,10 @@
 namespace smcrt {
 
 #define SMCRT_FULL 0xffffffffu
+// A branch a lane rarely takes (interfaces, launches, terminations, parking):
+// the compiler places its code away from the hot path of the packet loop,
+// which runs close to the instruction cache's capacity.
+#define SMCRT_RARE(x) __builtin_expect(!!(x), 0)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10, from its definition (Salmon, Moraes, Dror & Shaw, SC'11):
@@ -44,7 +48,9 @@ namespace smcrt {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
-#pragma unroll
+    // two rounds per trip: the packet loop's code must fit the instruction
+    // cache, and a fully unrolled generator is most of a kilobyte of it
+#pragma unroll 2
     for (int r = 0; r < 10; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
@@ -443,7 +449,8 @@ __device__ __forceinline__ Eval64 scene_eval64(const DevScene &S, double x, doub
 // Value of the culled fold region at p: the fold over the primitives listed
 // for p's cell, bounded by cull_rmax (every unlisted primitive is farther
 // than R from the cell, so it cannot change the value below that bound).
-__device__ __forceinline__ float culled_region32(const DevScene &S, float x, float y, float z)
+// Out of line: scenes without a culled region keep it out of the packet loop.
+static __device__ __noinline__ float culled_region32(const DevScene &S, float x, float y, float z)
 {
     const int g = S.cull_g;
     const int cx = __float2int_rd((x - S.cull_lo[0]) * S.cull_inv_s[0]);
@@ -472,6 +479,11 @@ __device__ __forceinline__ void region_end32(Eval32 *E, int r, float d, int sel,
     if (r == sel) E->dsel = d;
 }
 
+// One copy of the interpreter in the packet loop: the culled region's
+// instructions [cb, ce) are replaced by its culled distance inside the same
+// loop (each region's program is self-contained, so the stack left by the
+// regions before it does not matter).  Code size counts here: the loop runs
+// close to the instruction cache's capacity.
 template <bool G>
 __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float y, float z, int sel)
 {
@@ -479,15 +491,37 @@ __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float
     E.dmin = __int_as_float(0x7f800000);
     E.dsoft = E.dmin;
     E.dstar = 0.f; E.dsel = 0.f; E.istar = -1; E.region = -1;
-    if (S.cull_region < 0) {
-        run_prog32<true, G>(S, 0, S.ninstr, x, y, z, sel, &E);
-    } else {   // regions in index order: before, the culled one, after
+    int cb = S.ninstr, ce = S.ninstr;
+    if (S.cull_region >= 0) {
         const int2 rr = (*(S.rrange + S.cull_region));
-        run_prog32<true, G>(S, 0, rr.x, x, y, z, sel, &E);
-        // the culled region's distance always bounds segment moves
-        // isotropically (its primitives are not in seg_prims)
-        region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, true);
-        run_prog32<true, G>(S, rr.y, S.ninstr, x, y, z, sel, &E);
+        cb = rr.x;
+        ce = rr.y;
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int i = 0; i < S.ninstr; ++i) {
+        if (i == cb) {
+            // the culled region's distance always bounds segment moves
+            // isotropically (its primitives are not in seg_prims)
+            region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, true);
+            i = ce - 1;
+            continue;
+        }
+        const int4 ins = (*(reinterpret_cast<const int4 *>(S.instr) + i));
+        const int op = ins.x & 0xff, kind = (ins.x >> 8) & 0xff;
+        float v = 0.f;
+        if (ins.y >= 0) v = prim32<G>(S, kind, ins.y, x, y, z);
+        if (op == 0) {
+            s3 = s2; s2 = s1; s1 = s0; s0 = v;
+        } else {
+            const float kinv = __int_as_float(ins.w);
+            if (ins.y >= 0) {
+                s0 = csg32(op, s0, v, kinv);
+            } else {
+                s0 = csg32(op, s1, s0, kinv);
+                s1 = s2; s2 = s3;
+            }
+        }
+        if (ins.z >= 0) region_end32(&E, ins.z, s0, sel, (ins.x & kSoftRegionEnd) != 0);
     }
     const float db = box32(x, y, z, S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2]);
     E.dbox = db;

@@ -10,19 +10,22 @@ Both runs use segment stepping, as the benchmark does.  The oracle cannot run
 - FP64 kernel, on a random sample of the workload's packet ids: each
   packet's record (R, T, A, killed, gain, scatters, steps) equals the
   oracle's, one by one.
-- Mixed kernel, on all 1e8 packets:
-  - R/T/A agree with an independent oracle sample within 4 sigma of that
-    sample's error;
-  - the fluence map, summed over blocks of voxels, agrees with the sample's
-    map within the sample's own noise;
+- Mixed kernel, on all 1e8 packets (20 launches of 5e6 consecutive ids):
+  - R/T/A agree with an independent oracle sample within 3 sigma of the
+    combined error;
+  - the fluence map, block by block: one z per voxel block from the batch
+    spreads of both sides (Welch), accepted by ``bench.block_stats``;
   - energy closes;
   - no packet reaches the step cap.
+The paired comparison with the FP64 kernel on the same ids is in
+``test_gpu_parity_blocks.py``.
 """
 import math
 
 import numpy as np
 import pytest
 
+import bench
 import oracle as O
 import paper_2112_08035_gb300 as smc
 import workloads as W
@@ -34,8 +37,8 @@ RECORD_KEYS = ("R", "T", "A", "killed", "gain", "scatters", "steps")
 
 # (workload, voxel block side for the coarse map, oracle sample size)
 CASES = [
-    ("vessel_network", lambda: W.vessel_network(), 10, 20000),
-    ("glass_container", lambda: W.glass_container(), 8, 40000),
+    ("vessel_network", lambda: W.vessel_network(), 40, 20000),
+    ("glass_container", lambda: W.glass_container(), 16, 40000),
 ]
 
 
@@ -44,11 +47,6 @@ def ctx():
     c = smc.Context(0)
     yield c
     c.close()
-
-
-def _coarse(f, b):
-    nz, ny, nx = f.shape
-    return f.reshape(nz // b, b, ny // b, b, nx // b, b).sum(axis=(1, 3, 5))
 
 
 @pytest.mark.parametrize("name,make,block,nsample", CASES, ids=[c[0] for c in CASES])
@@ -80,44 +78,48 @@ def test_fp64_sampled_packets_full_size(ctx, name, make, block, nsample):
 @pytest.mark.parametrize("name,make,block,nsample", CASES, ids=[c[0] for c in CASES])
 def test_mixed_full_size_against_oracle_sample(ctx, name, make, block, nsample):
     import torch
+    pytest.importorskip("scipy")
     wl = make().with_stepping(W.SEGMENT)
     N = wl.npackets
+    K = 20
+    per = N // K
     g = wl.grid
     plan = ctx.plan(wl, "mixed")
     flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
+    acc = torch.zeros_like(flu)
     tot = smc.totals_tensor()
-    plan.launch(0, N, wl.seed, flu, tot)
+    bg = []
+    for k in range(K):
+        flu.zero_()
+        plan.launch(k * per, per, wl.seed, flu, tot)
+        acc += flu
+        bg.append(bench.block_sums(flu, (block,) * 3) / FX / per)
     torch.cuda.synchronize()
     assert plan.status() == 0
     plan.close()
     t = smc.totals_from_tensor(tot)
-    fg = flu.cpu().numpy()
-    del flu
+    assert int(acc.min()) >= 0
+    del flu, acc
     torch.cuda.empty_cache()
     assert t["packets"] == N
     assert t["max_steps_hit"] == 0, t["max_steps_hit"]
     bal = (t["R"] + t["T"] + t["A"] + t["killed"] - t["gain"]) / FX
     assert abs(bal - N) < 1e-4 * N, (bal, N)
-    assert fg.min() >= 0
 
     # independent oracle sample: packet ids far from the GPU's [0, N), in
-    # two halves whose difference measures the sample's own noise
-    h = nsample // 2
+    # K batches
+    po = nsample // K
     base = 4 * N
-    fo1, _, r1 = O.run(wl.with_packets(h), base, records=True)
-    fo2, _, r2 = O.run(wl.with_packets(h), base + h, records=True)
-    ro = np.concatenate([r1, r2])
+    ro, bo = [], []
+    for k in range(K):
+        fo, _, r = O.run(wl.with_packets(po), base + k * po, records=True)
+        ro.append(r)
+        bo.append(bench.block_sums(fo, (block,) * 3) / FX / po)
+    ro = np.concatenate(ro)
     for k in ("R", "T", "A"):
         x = ro[k].astype(np.float64) / FX
         se = math.sqrt(x.var() / x.size * (1.0 + x.size / N))
         z = abs(t[k] / FX / N - x.mean()) / max(se, 1e-12)
-        assert z < 4.0, (name, k, t[k] / FX / N, x.mean(), se, z)
-
-    cg = _coarse(fg, block) / FX / N
-    c1 = _coarse(fo1, block) / FX / h
-    c2 = _coarse(fo2, block) / FX / h
-    co = 0.5 * (c1 + c2)
-    # the sample of nsample packets has about 1/sqrt(2) of one half's noise
-    noise = np.linalg.norm(c1 - c2) / math.sqrt(2) / np.linalg.norm(co) / math.sqrt(2)
-    l2 = np.linalg.norm(cg - co) / np.linalg.norm(co)
-    assert l2 < 3.0 * noise + 1e-3, (name, l2, noise)
+        assert z < 3.0, (name, k, t[k] / FX / N, x.mean(), se, z)
+    s = bench.block_stats(np.array(bg), np.array(bo), paired=False)
+    assert s["blocks"] >= 8 and s["pass"], (name, s)

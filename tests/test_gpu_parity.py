@@ -4,8 +4,11 @@ FP64 mode: the kernel performs the oracle's IEEE operations in the same
 order, so every int64 tally (fluence voxels, R, T, A, killed, gain,
 scatter and step counts) and every per-packet record must be IDENTICAL.
 Mixed mode: a different but consistent estimator of the same transport, so
-R, T, A and the fluence must agree with the oracle within Monte Carlo error
-(z-score over per-packet variances; 4 sigma).
+R, T, A and the fluence must agree with the oracle within Monte Carlo error:
+R, T, A within 3 sigma (z over per-packet variances); the fluence block by
+block over the whole map, from batch spreads on both sides
+(``bench.block_stats``).  The paired comparison with the FP64 kernel at
+millions of packets is in ``test_gpu_parity_blocks.py``.
 """
 import math
 from dataclasses import replace
@@ -13,6 +16,7 @@ from dataclasses import replace
 import numpy as np
 import pytest
 
+import bench
 import oracle as O
 import paper_2112_08035_gb300 as smc
 import workloads as W
@@ -133,7 +137,7 @@ def test_fp64_id_offset_and_split_additivity(ctx):
         assert ta[k] + tb[k] == to[k]
 
 
-def _zcheck(rg, ro, key, k=4.0):
+def _zcheck(rg, ro, key, k=3.0):
     a = rg[key].astype(np.float64) / FX
     b = ro[key].astype(np.float64) / FX
     se = math.sqrt(a.var() / a.size + b.var() / b.size)
@@ -142,36 +146,65 @@ def _zcheck(rg, ro, key, k=4.0):
     return z
 
 
+# (factory, GPU packets, oracle packets, voxel block edge)
 MIXED = [
-    (W.sphere_pencil, 200_000, 20_000),
-    (W.three_layer_slab, 200_000, 10_000),
-    (W.vessel_network, 40_000, 2_000),
-    (W.vessel_network_hard, 40_000, 2_000),
-    (W.glass_container, 100_000, 5_000),
+    (W.sphere_pencil, 200_000, 20_000, 5),
+    (W.three_layer_slab, 200_000, 10_000, 10),
+    (W.vessel_network, 40_000, 2_000, 50),
+    (W.vessel_network_hard, 40_000, 2_000, 25),
+    (W.glass_container, 100_000, 5_000, 16),
 ]
+NBATCH = 20
+
+
+def gpu_batches(ctx, wl, precision, n, K, block, id_begin):
+    """K launches of n // K consecutive ids from id_begin: per-packet
+    records and per-batch block sums of the fluence (per packet)."""
+    torch = _torch()
+    plan = ctx.plan(wl, precision)
+    g = wl.grid
+    per = n // K
+    flu = torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda")
+    tot = smc.totals_tensor()
+    rec = torch.zeros(K * per * 8, dtype=torch.int64, device="cuda")
+    blocks = []
+    for k in range(K):
+        flu.zero_()
+        plan.launch(id_begin + k * per, per, wl.seed, flu, tot, rec[k * per * 8:(k + 1) * per * 8])
+        blocks.append(bench.block_sums(flu, (block,) * 3) / FX / per)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    plan.close()
+    return rec.cpu().numpy().view(smc.RECORD_DTYPE), np.array(blocks)
+
+
+def oracle_batches(wl, n, K, block, id_begin=0):
+    """The oracle on K batches of n // K consecutive ids: records and
+    per-batch block sums (per packet)."""
+    per = n // K
+    recs, blocks = [], []
+    for k in range(K):
+        f, _, r = O.run(wl.with_packets(per), id_begin + k * per, records=True)
+        recs.append(r)
+        blocks.append(bench.block_sums(f, (block,) * 3) / FX / per)
+    return np.concatenate(recs), np.array(blocks)
 
 
 @pytest.mark.parametrize("stepping", [W.SPHERE_TRACING, W.SEGMENT])
-@pytest.mark.parametrize("factory,ng,no", MIXED, ids=[f.__name__ for f, _, _ in MIXED])
-def test_mixed_matches_oracle_statistically(ctx, factory, ng, no, stepping):
+@pytest.mark.parametrize("factory,ng,no,block", MIXED, ids=[f.__name__ for f, _, _, _ in MIXED])
+def test_mixed_matches_oracle_statistically(ctx, factory, ng, no, block, stepping):
+    pytest.importorskip("scipy")
     # the oracle always runs the paper's plain sphere tracing; the GPU runs
     # mixed precision with either step rule
     wl = factory()
-    fo, to, ro = O.run(wl.with_packets(no), records=True)
+    ro, bo = oracle_batches(wl, no, NBATCH, block)
     # disjoint packet ids for the GPU sample: independent estimates
-    fg, tg, rg = run_gpu(ctx, wl.with_packets(ng).with_stepping(stepping), "mixed", records=True,
-                         id_begin=10_000_000)
+    rg, bg = gpu_batches(ctx, wl.with_stepping(stepping), "mixed", ng, NBATCH, block, 10_000_000)
     for key in ("R", "T", "A"):
         _zcheck(rg, ro, key)
-    # fluence: relative L2 difference of the normalised maps is consistent
-    # with the oracle's own noise (compare against half-sample noise)
-    po = fo / FX / no
-    pg = fg / FX / ng
-    l2 = np.linalg.norm(pg - po) / np.linalg.norm(po)
-    fo1, _, _ = O.run(wl.with_packets(no // 2), 20_000_000)
-    fo2, _, _ = O.run(wl.with_packets(no // 2), 30_000_000)
-    noise = np.linalg.norm(fo1 / (no // 2) - fo2 / (no // 2)) / FX / np.linalg.norm(po) / math.sqrt(2)
-    assert l2 < 2.5 * noise + 1e-3, (l2, noise)
+    # fluence: a z per voxel block over the whole map (Welch, batch spreads)
+    s = bench.block_stats(bg, bo, paired=False)
+    assert s["blocks"] >= 8 and s["pass"], s
     # energy closes per packet (FP32 weights: relative 1e-5 per packet)
     bal = (rg["R"] + rg["T"] + rg["A"] + rg["killed"] - rg["gain"]) / FX
     assert np.all(np.abs(bal - 1.0) < 1e-4)
@@ -336,7 +369,8 @@ def test_fp64_bitexact_iso_source_and_roulette(ctx):
 def test_full_size_three_layer_sampled(ctx):
     """The 1e7-packet layered workload in its benchmark launch shape: FP64
     per-packet records of a random sample of ids equal the oracle's one by
-    one; mixed-mode R/T/A agree with the FP64 run within MC error."""
+    one; mixed-mode R/T/A agree with the FP64 run on the same ids within
+    3 sigma of their paired differences."""
     torch = _torch()
     wl = W.three_layer_slab()
     fg, tg, rg = run_gpu(ctx, wl, "fp64", records=True)
@@ -349,7 +383,8 @@ def test_full_size_three_layer_sampled(ctx):
             assert rg[f][i] == ro[f][0], (i, f)
     fm, tm, rm = run_gpu(ctx, wl, "mixed", records=True)
     assert tm["packets"] == wl.npackets
-    for key in ("R", "T", "A"):
-        _zcheck(rm, rg, key)
+    for key in ("R", "T", "A"):   # paired on the same 1e7 ids, 3 sigma
+        z = bench.paired_z(rm[key] / FX, rg[key] / FX)
+        assert abs(z) < 3.0, (key, z)
     del rg, rm
     torch.cuda.empty_cache()
