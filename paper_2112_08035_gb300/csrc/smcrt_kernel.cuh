@@ -449,8 +449,7 @@ __device__ __forceinline__ Eval64 scene_eval64(const DevScene &S, double x, doub
 // Value of the culled fold region at p: the fold over the primitives listed
 // for p's cell, bounded by cull_rmax (every unlisted primitive is farther
 // than R from the cell, so it cannot change the value below that bound).
-// Out of line: scenes without a culled region keep it out of the packet loop.
-static __device__ __noinline__ float culled_region32(const DevScene &S, float x, float y, float z)
+__device__ __forceinline__ float culled_region32(const DevScene &S, float x, float y, float z)
 {
     const int g = S.cull_g;
     const int cx = __float2int_rd((x - S.cull_lo[0]) * S.cull_inv_s[0]);
@@ -483,7 +482,8 @@ __device__ __forceinline__ void region_end32(Eval32 *E, int r, float d, int sel,
 // instructions [cb, ce) are replaced by its culled distance inside the same
 // loop (each region's program is self-contained, so the stack left by the
 // regions before it does not matter).  Code size counts here: the loop runs
-// close to the instruction cache's capacity.
+// close to the instruction cache's capacity (measured on the layered slab:
+// three interpreter copies 203.6 ms per 1e7 packets, one copy 184.4 ms).
 template <bool G>
 __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float y, float z, int sel)
 {
