@@ -627,7 +627,7 @@ def main():
     # baseline, the reference for the accuracy fields, and the algorithmic
     # work counts of the roofline
     if args.quick or world > 1:
-        counts = O.run(wl.with_packets(20_000), fluence=False)[1]
+        counts = O.run(wl.with_packets(20_000), fluence=True)[1]
         osamp = None
     else:
         log("oracle leg")

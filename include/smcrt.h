@@ -48,10 +48,16 @@ extern "C" {
 #define SMCRT_ERR_BAD_SCENE -2    /* scene / source / grid failed validation */
 #define SMCRT_ERR_NO_MEMORY -3    /* device or host allocation failed, or over budget */
 #define SMCRT_ERR_CUDA -4         /* a CUDA runtime call failed */
-#define SMCRT_ERR_TIMEOUT -5      /* smcrt_wait timed out (job keeps running) */
+#define SMCRT_ERR_TIMEOUT -5      /* smcrt_wait timed out (job keeps running), or a launch's
+                                     device time limit expired (smcrt_set_time_limit) */
 #define SMCRT_ERR_CANCELLED -6    /* job was cancelled */
 #define SMCRT_ERR_NOT_FOUND -7    /* unknown job id */
 #define SMCRT_ERR_DEVICE -8       /* kernel reported an error status word */
+
+/* ---- bits of the kernels' status word (smcrt_plan_status) ------------- */
+#define SMCRT_STATUS_BAD_JOB 1    /* a launch descriptor without scene or totals, or a scene
+                                     that needs the general-shape kernel */
+#define SMCRT_STATUS_TIMEOUT 4    /* the launch's device time limit expired */
 
 /* ---- scene description (Sec. 2.2-2.3) ---------------------------------- */
 enum smcrt_prim_kind {
@@ -290,8 +296,26 @@ int smcrt_plan_launch(smcrt_plan *plan, uint64_t id_begin, uint64_t npackets, ui
 int smcrt_plan_set_variant(smcrt_plan *plan, int32_t variant);
 
 /* Read back the kernel's device error word for the plan's last launches
- * (0 = none) and clear it. */
+ * (0 = none; SMCRT_STATUS_* bits) and clear it. */
 int smcrt_plan_status(smcrt_plan *plan, int32_t *status);
+
+/* Device time limit of the plan's later launches (seconds; 0 = none, the
+ * default is the context's, smcrt_set_time_limit).  Each warp of the packet
+ * kernel reads the GPU's global nanosecond timer when it claims new packet
+ * ids; once the limit has passed since it started on the launch it claims no
+ * more, lets the packets it holds finish (each bounded by the step cap) and
+ * returns, and the kernel sets SMCRT_STATUS_TIMEOUT in the status word.  The
+ * totals and the fluence then cover exactly the packets that completed
+ * (totals.packets of them; R + T + A + killed - gain closes over those).
+ * The paper has no counterpart: this bounds a launch's time on the device.
+ * Errors: BAD_ARG for a negative or non-finite value. */
+int smcrt_plan_set_time_limit(smcrt_plan *plan, double seconds);
+
+/* The context's device time limit (seconds, 0 = none): applied to smcrt_run,
+ * which then returns SMCRT_ERR_TIMEOUT (and writes nothing) when it expires,
+ * and the default of plans created afterwards.  Serving rounds are bounded by
+ * their own budgets and do not use it. */
+int smcrt_set_time_limit(smcrt_ctx *ctx, double seconds);
 
 /* Time the candidate launch shapes (register-budget variant x, for MIXED
  * plans, scene tables in global or shared memory x threads per block x

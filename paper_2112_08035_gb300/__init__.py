@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "_build", f"libsmcrt_{platform.machine()}.so")
 OK, ERR_BAD_ARG, ERR_BAD_SCENE, ERR_NO_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_CANCELLED, ERR_NOT_FOUND, ERR_DEVICE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 FP64, MIXED = 0, 1
+STATUS_BAD_JOB, STATUS_TIMEOUT = 1, 4   # kernel status word bits (Plan.status)
 FX = 2.0 ** 32
 
 _PRIM_KIND = {"sphere": 0, "box": 1, "capsule": 2, "torus": 3, "cylinder": 4}
@@ -130,6 +131,8 @@ def lib():
                 "smcrt_plan_status": (C.c_int, [vp, C.POINTER(i32)]),
                 "smcrt_plan_autotune": (C.c_int, [vp, u64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
                 "smcrt_plan_set_variant": (C.c_int, [vp, i32]),
+                "smcrt_plan_set_time_limit": (C.c_int, [vp, C.c_double]),
+                "smcrt_set_time_limit": (C.c_int, [vp, C.c_double]),
                 "smcrt_run": (C.c_int, [vp, C.POINTER(Scene), C.POINTER(Source), C.POINTER(Grid), u64, u64,
                                         i32, vp, C.POINTER(Totals)]),
                 "smcrt_submit": (C.c_int, [vp, C.POINTER(Scene), C.POINTER(Source), C.POINTER(Grid), u64, u64,
@@ -244,6 +247,10 @@ class Plan:
     def set_variant(self, variant):
         _check(lib().smcrt_plan_set_variant(self.h, int(variant)), "plan_set_variant")
 
+    def set_time_limit(self, seconds):
+        """Device time limit of later launches (0 = none); see status()."""
+        _check(lib().smcrt_plan_set_time_limit(self.h, float(seconds)), "plan_set_time_limit")
+
     def autotune(self, trial_packets):
         """Returns the chosen (blocks, threads, variant)."""
         b, t, v = C.c_int32(), C.c_int32(), C.c_int32()
@@ -285,6 +292,10 @@ class Context:
 
     def plan(self, wl, precision="mixed") -> Plan:
         return Plan(self, wl, precision)
+
+    def set_time_limit(self, seconds):
+        """Device time limit of run() and the default of later plans (0 = none)."""
+        _check(lib().smcrt_set_time_limit(self.h, float(seconds)), "set_time_limit")
 
     def run(self, wl, precision=None, fluence=True, out=None):
         """Synchronous run of packets [0, wl.npackets).  Returns (fluence

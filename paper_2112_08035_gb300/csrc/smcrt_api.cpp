@@ -228,6 +228,7 @@ struct smcrt_ctx {
     int device = 0;
     int sm_count = 0;
     size_t budget = 0;
+    double time_limit_s = 0.0;   // device time limit of smcrt_run and the default of new plans
     std::mutex tune_mu;
     struct Tuned { int blocks, threads, variant; };
     std::map<uint64_t, Tuned> tuned;  // scene shape -> launch shape
@@ -259,6 +260,7 @@ struct smcrt_plan {
     int *dstatus = nullptr;
     int blocks = 0, threads = 0, variant = 0;
     int stage = 0;             // mixed: stage the scene tables in shared memory
+    double time_limit_s = 0.0; // device time limit of a launch (0 = none)
     size_t cells = 0;
     size_t dbytes = 0;
     uint64_t shape_key = 0;
@@ -610,6 +612,7 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     }
     pl->cells = (size_t)g->n[0] * g->n[1] * g->n[2];
     pl->shape_key = shape_key(sc, precision, g);
+    pl->time_limit_s = ctx->time_limit_s;
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tuned.find(pl->shape_key);
@@ -648,6 +651,7 @@ int plan_launch_impl(smcrt_plan *pl, uint64_t id_begin, uint64_t n, uint64_t see
     jw.scene = pl->dscene;
     jw.cancelled = 0;
     jw.stage = pl->precision == SMCRT_MIXED ? pl->stage : 0;
+    jw.time_limit_ns = pl->time_limit_s > 0.0 ? (unsigned long long)std::llround(pl->time_limit_s * 1e9) : 0ull;
     JobWork *slot = pl->djobs + pl->ring_pos;
     pl->ring_pos = (pl->ring_pos + 1) % pl->ring;
     if (launch_set_job(slot, jw, s) != cudaSuccess) return SMCRT_ERR_CUDA;
@@ -772,27 +776,44 @@ void scheduler(smcrt_ctx *ctx)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     chk(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming), SMCRT_ERR_CUDA);
     chk(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming), SMCRT_ERR_CUDA);
-    int *d_status = nullptr;
+    // Status words: one per round buffer for the launch (cleared by the
+    // round's graph before its kernels run), and one per job slot (cleared
+    // when a job is admitted to the slot), both read back with the totals:
+    // a job that the kernel flags fails alone, and no flag outlives its round.
+    int *d_status = nullptr;     // [kRoundsInFlight]
+    int32_t *d_jstat = nullptr;  // [kMaxSlots]
     smcrt_totals *d_tot = nullptr;
-    chk(inject ? cudaErrorMemoryAllocation : cudaMalloc(&d_status, sizeof(int)), SMCRT_ERR_NO_MEMORY);
-    if (d_status) chk(cudaMemset(d_status, 0, sizeof(int)), SMCRT_ERR_CUDA);
+    chk(inject ? cudaErrorMemoryAllocation : cudaMalloc(&d_status, sizeof(int) * kRoundsInFlight),
+        SMCRT_ERR_NO_MEMORY);
+    if (d_status) chk(cudaMemset(d_status, 0, sizeof(int) * kRoundsInFlight), SMCRT_ERR_CUDA);
+    chk(cudaMalloc(&d_jstat, sizeof(int32_t) * kMaxSlots), SMCRT_ERR_NO_MEMORY);
+    if (d_jstat) chk(cudaMemset(d_jstat, 0, sizeof(int32_t) * kMaxSlots), SMCRT_ERR_CUDA);
     chk(cudaMalloc(&d_tot, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_NO_MEMORY);
     if (d_tot) chk(cudaMemset(d_tot, 0, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_CUDA);
-    int *h_status = nullptr;
-    chk(cudaMallocHost(&h_status, sizeof(int)), SMCRT_ERR_NO_MEMORY);
-    const int threads = 128;
-    const int occ_m = std::max(1, occupancy_mixed(threads, default_variant(SMCRT_MIXED))),
-              occ_d = std::max(1, occupancy_fp64(threads, default_variant(SMCRT_FP64)));
-    const int blocks_m = ctx->sm_count * occ_m, blocks_d = ctx->sm_count * occ_d;
+    // Launch shape of the served kernels.  The mixed kernel's register
+    // variant, scene-table staging, threads and blocks are chosen by timing
+    // trials on the first mixed job served (tune_served below) before the
+    // graphs are captured; until then, and for FP64, the defaults.
+    int threads_m = 128, variant_m = default_variant(SMCRT_MIXED), stage_m = 1;
+    int blocks_m = ctx->sm_count * std::max(1, occupancy_mixed(threads_m, variant_m));
+    const int threads_d = 128;
+    const int blocks_d = ctx->sm_count * std::max(1, occupancy_fp64(threads_d, default_variant(SMCRT_FP64)));
+    bool tuned_served = false;
     int clk_khz = 1900000;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, ctx->device);
     // warp-cycles one round can spend (the mixed kernel's resident warps)
-    const double round_cycles = (double)blocks_m * (threads / 32) * clk_khz * 1e3 * kRoundSeconds;
+    auto round_cycles = [&] { return (double)blocks_m * (threads_m / 32) * clk_khz * 1e3 * kRoundSeconds; };
     const long long park_cycles = (long long)(clk_khz * 1e3 * kParkSeconds);
+    // SMCRT_FAULT_BAD_JOB=<job id>: that job's round-table entry gets no
+    // scene, which the kernels report as a bad job (host-side injection for
+    // the status tests; no GPU fault is involved).
+    uint64_t bad_job = 0;
+    if (const char *bj = std::getenv("SMCRT_FAULT_BAD_JOB")) bad_job = std::strtoull(bj, nullptr, 10);
 
     struct Buf {
         JobWork *h_tab = nullptr, *d_tab = nullptr;   // [2 * kMaxSlots]: mixed table, then FP64 table
         smcrt_totals *h_tot = nullptr;                // totals snapshot taken at the end of the round
+        int32_t *h_stat = nullptr;                    // [1 + kMaxSlots]: the round's status, then each slot's
         cudaGraphExec_t graph = nullptr;     // plain scenes only
         cudaGraphExec_t graph_g = nullptr;   // kernels for scenes with general shapes
         cudaEvent_t ev = nullptr, ev0 = nullptr;
@@ -808,30 +829,117 @@ void scheduler(smcrt_ctx *ctx)
         chk(cudaMallocHost(&b.h_tab, sizeof(JobWork) * 2 * kMaxSlots), SMCRT_ERR_NO_MEMORY);
         chk(cudaMalloc(&b.d_tab, sizeof(JobWork) * 2 * kMaxSlots), SMCRT_ERR_NO_MEMORY);
         chk(cudaMallocHost(&b.h_tot, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_NO_MEMORY);
+        chk(cudaMallocHost(&b.h_stat, sizeof(int32_t) * (1 + kMaxSlots)), SMCRT_ERR_NO_MEMORY);
         chk(cudaEventCreate(&b.ev), SMCRT_ERR_CUDA);
         chk(cudaEventCreate(&b.ev0), SMCRT_ERR_CUDA);
         if (setup_rc != SMCRT_OK) break;
         std::memset(b.h_tab, 0, sizeof(JobWork) * 2 * kMaxSlots);
-        for (int gen = 0; gen < 2; ++gen) {
-            const int off = gen ? kNumVariants : 0;
-            cudaGraph_t g;
-            cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-            cudaMemcpyAsync(b.d_tab, b.h_tab, sizeof(JobWork) * 2 * kMaxSlots, cudaMemcpyHostToDevice, st);
-            launch_round_prologue(b.d_tab, 2 * kMaxSlots, st);
-            cudaEventRecord(ev_fork, st);
-            cudaStreamWaitEvent(st2, ev_fork, 0);
-            launch_mixed(b.d_tab, kMaxSlots, d_status, blocks_m, threads, st, default_variant(SMCRT_MIXED) + off);
-            launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status, blocks_d, threads, st2,
-                        default_variant(SMCRT_FP64) + off);
-            cudaEventRecord(ev_join, st2);
-            cudaStreamWaitEvent(st, ev_join, 0);
-            cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
-            chk(cudaStreamEndCapture(st, &g), SMCRT_ERR_CUDA);
-            if (setup_rc != SMCRT_OK) break;
-            chk(cudaGraphInstantiate(gen ? &b.graph_g : &b.graph, g, 0), SMCRT_ERR_CUDA);
-            cudaGraphDestroy(g);
-        }
+        std::memset(b.h_stat, 0, sizeof(int32_t) * (1 + kMaxSlots));
     }
+
+    // Capture each buffer's round graphs with the current launch shape.
+    auto capture = [&]() -> int {
+        for (int bi = 0; bi < kRoundsInFlight; ++bi) {
+            Buf &b = buf[bi];
+            for (int gen = 0; gen < 2; ++gen) {
+                const int off = gen ? kNumVariants : 0;
+                cudaGraph_t g;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMCRT_ERR_CUDA;
+                cudaMemsetAsync(d_status + bi, 0, sizeof(int), st);
+                cudaMemcpyAsync(b.d_tab, b.h_tab, sizeof(JobWork) * 2 * kMaxSlots, cudaMemcpyHostToDevice, st);
+                launch_round_prologue(b.d_tab, 2 * kMaxSlots, st);
+                cudaEventRecord(ev_fork, st);
+                cudaStreamWaitEvent(st2, ev_fork, 0);
+                launch_mixed(b.d_tab, kMaxSlots, d_status + bi, blocks_m, threads_m, st, variant_m + off);
+                launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status + bi, blocks_d, threads_d, st2,
+                            default_variant(SMCRT_FP64) + off);
+                cudaEventRecord(ev_join, st2);
+                cudaStreamWaitEvent(st, ev_join, 0);
+                cudaMemcpyAsync(b.h_tot, d_tot, sizeof(smcrt_totals) * kMaxSlots, cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(b.h_stat, d_status + bi, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(b.h_stat + 1, d_jstat, sizeof(int32_t) * kMaxSlots, cudaMemcpyDeviceToHost, st);
+                if (cudaStreamEndCapture(st, &g) != cudaSuccess) return SMCRT_ERR_CUDA;
+                cudaGraphExec_t &ge = gen ? b.graph_g : b.graph;
+                if (ge) cudaGraphExecDestroy(ge);
+                ge = nullptr;
+                const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return SMCRT_ERR_CUDA;
+            }
+        }
+        return SMCRT_OK;
+    };
+    if (setup_rc == SMCRT_OK) setup_rc = capture();
+
+    // Timing trials of the served mixed kernel on one job's scene (scratch
+    // tallies, ids from 0 with the job's seed): register variant x scene
+    // tables in global or shared memory x threads x resident blocks, as
+    // smcrt_plan_autotune does for a plan.  Results do not depend on the
+    // choice (every variant computes the same bits).
+    auto tune_served = [&](const Job &j) {
+        const uint64_t trial = std::min<uint64_t>(j.npackets, 50000);
+        const size_t cells = (size_t)j.grid.n[0] * j.grid.n[1] * j.grid.n[2];
+        void *flu = nullptr, *tot = nullptr, *tab = nullptr, *tst = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = cudaMallocAsync(&flu, cells * 8, st) == cudaSuccess &&
+                  cudaMallocAsync(&tot, sizeof(smcrt_totals), st) == cudaSuccess &&
+                  cudaMallocAsync(&tab, sizeof(JobWork), st) == cudaSuccess &&
+                  cudaMallocAsync(&tst, sizeof(int), st) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+        const int off = j.plan->host.general ? kNumVariants : 0;
+        float best = 1e30f;
+        for (int pv = 0; ok && pv < 2 * kNumVariants; ++pv) {
+            const int v = pv % kNumVariants, stage = pv / kNumVariants;
+            for (int t : {64, 128}) {
+                const int occ = occupancy_mixed(t, v + off);
+                if (occ < 1) continue;
+                for (int mult : {1, 2}) {
+                    const int b = ctx->sm_count * occ * mult;
+                    JobWork w{};
+                    w.next = 0;
+                    w.end = trial;
+                    w.begin = 0;
+                    w.seed = j.seed;
+                    w.fluence = (long long *)flu;
+                    w.totals = (smcrt_totals *)tot;
+                    w.scene = j.plan->dscene;
+                    w.stage = stage;
+                    cudaMemsetAsync(flu, 0, cells * 8, st);
+                    cudaMemsetAsync(tot, 0, sizeof(smcrt_totals), st);
+                    if (launch_set_job((JobWork *)tab, w, st) != cudaSuccess) { ok = false; break; }
+                    cudaEventRecord(e0, st);
+                    if (launch_mixed((JobWork *)tab, 1, (int *)tst, b, t, st, v + off) != cudaSuccess) {
+                        ok = false;
+                        break;
+                    }
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        variant_m = v;
+                        stage_m = stage;
+                        threads_m = t;
+                        blocks_m = b;
+                    }
+                }
+                if (!ok) break;
+            }
+        }
+        if (flu) cudaFreeAsync(flu, st);
+        if (tot) cudaFreeAsync(tot, st);
+        if (tab) cudaFreeAsync(tab, st);
+        if (tst) cudaFreeAsync(tst, st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaGetLastError();
+        if (trace)
+            std::fprintf(stderr, "[smcrt] served kernel tuned on job %llu: variant %d stage %d threads %d blocks %d\n",
+                         (unsigned long long)j.id, variant_m, stage_m, threads_m, blocks_m);
+        return ok;
+    };
+
     if (setup_rc != SMCRT_OK) {
         // fail every queued job, and every later one, until the context ends
         std::unique_lock<std::mutex> lk(ctx->mu);
@@ -913,6 +1021,7 @@ void scheduler(smcrt_ctx *ctx)
             if (rc == SMCRT_OK) {
                 cudaMemsetAsync(j->dflu, 0, fb, st);
                 cudaMemsetAsync(d_tot + j->slot, 0, sizeof(smcrt_totals), st);
+                cudaMemsetAsync(d_jstat + j->slot, 0, sizeof(int32_t), st);
                 active.push_back(j);
             } else {
                 free_job_device(*j, st);
@@ -940,7 +1049,9 @@ void scheduler(smcrt_ctx *ctx)
                              (long long)B.idx, B.njobs, (unsigned long long)B.quanta, ms,
                              1e3 * (now_s() - B.t_launch), parked);
             }
-            cudaMemcpy(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+            // the round's launch status: bits that name no job fail the jobs
+            // the round carried; a job's own status word fails that job alone
+            const int rstat = B.h_stat[0] & ~kStatusBadJob;
             std::vector<std::shared_ptr<Job>> still;
             for (auto &j : active) {
                 if (B.idx < j->admit_round) {
@@ -950,8 +1061,11 @@ void scheduler(smcrt_ctx *ctx)
                 const smcrt_totals &t = B.h_tot[j->slot];
                 if (t.packets > 0 && t.busy_cycles > 0) j->cost = (double)t.busy_cycles / (double)t.packets;
                 const bool drained = j->last_round <= completed;
-                if ((uint64_t)t.packets >= j->npackets) {
-                    complete(j, &t, *h_status ? SMCRT_ERR_DEVICE : SMCRT_OK);
+                const bool failed = B.h_stat[1 + j->slot] != 0 || (rstat != 0 && j->last_round >= B.idx);
+                if (failed) {
+                    complete(j, &t, SMCRT_ERR_DEVICE);
+                } else if ((uint64_t)t.packets >= j->npackets) {
+                    complete(j, &t, SMCRT_OK);
                 } else if (drained && is_cancelled(j)) {
                     complete(j, &t, SMCRT_ERR_CANCELLED);
                 } else {
@@ -980,6 +1094,33 @@ void scheduler(smcrt_ctx *ctx)
             if (buf[1 - cur].busy) cur = 1 - cur;   // reap the other round next
             continue;
         }
+        if (!tuned_served) {
+            // the first mixed job served sets the served kernel's launch shape
+            const Job *first = nullptr;
+            for (auto &j : runnable)
+                if (j->precision == SMCRT_MIXED) { first = j.get(); break; }
+            if (first != nullptr) {
+                cudaStreamSynchronize(st);   // no round in flight while the graphs are replaced
+                tuned_served = true;
+                if (tune_served(*first)) {
+                    const int rc = capture();
+                    if (rc != SMCRT_OK) {
+                        // keep serving with the default shape captured at set-up
+                        variant_m = default_variant(SMCRT_MIXED);
+                        threads_m = 128;
+                        stage_m = 1;
+                        blocks_m = ctx->sm_count * std::max(1, occupancy_mixed(threads_m, variant_m));
+                        if (capture() != SMCRT_OK) {
+                            for (auto &j : active) complete(j, nullptr, SMCRT_ERR_CUDA);
+                            active.clear();
+                            std::lock_guard<std::mutex> lk(ctx->mu);
+                            ctx->sched_error = SMCRT_ERR_CUDA;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
         double known = 0;
         int nk = 0;
         int nfresh = 0;
@@ -988,7 +1129,7 @@ void scheduler(smcrt_ctx *ctx)
             if (j->cursor < j->npackets) ++nfresh;
         }
         const double dflt = nk ? known / nk : 2.0e5;
-        const double share = round_cycles / (double)std::max(1, nfresh);
+        const double share = round_cycles() / (double)std::max(1, nfresh);
         int nm = 0, nd = 0;
         bool general = false;
         for (auto &j : runnable) {
@@ -1005,12 +1146,13 @@ void scheduler(smcrt_ctx *ctx)
             w.fluence = (long long *)j->dflu;
             w.totals = d_tot + j->slot;
             w.records = nullptr;
-            w.scene = j->plan->dscene;
+            w.scene = j->id == bad_job ? nullptr : j->plan->dscene;
             w.cancelled = 0;
             w.park_cycles = park_cycles;
+            w.jstat = d_jstat + j->slot;
             w.defer = j->ddefer;
             w.defer_in = (int32_t)(issued & 1);
-            w.stage = j->precision == SMCRT_MIXED ? 1 : 0;
+            w.stage = j->precision == SMCRT_MIXED ? stage_m : 0;
             j->cursor += q;
             j->last_round = issued;
             if (j->precision == SMCRT_FP64) B.h_tab[kMaxSlots + nd++] = w;
@@ -1032,6 +1174,19 @@ void scheduler(smcrt_ctx *ctx)
         }
         cur = 1 - cur;
     }
+    {   // a scheduler that stopped on an error fails what is still queued
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->sched_error != SMCRT_OK && setup_rc == SMCRT_OK) {
+            while (!ctx->queue.empty()) {
+                auto j = ctx->queue.front();
+                ctx->queue.pop_front();
+                j->status = ctx->sched_error;
+                j->done = true;
+                j->t_done = now_s();
+            }
+            ctx->cv_done.notify_all();
+        }
+    }
     // shut down: wait for rounds, free everything still held
     if (st) cudaStreamSynchronize(st);
     for (auto &j : active) free_job_device(*j, st);
@@ -1049,9 +1204,10 @@ void scheduler(smcrt_ctx *ctx)
         if (b.ev0) cudaEventDestroy(b.ev0);
         if (b.h_tab) cudaFreeHost(b.h_tab);
         if (b.h_tot) cudaFreeHost(b.h_tot);
+        if (b.h_stat) cudaFreeHost(b.h_stat);
         if (b.d_tab) cudaFree(b.d_tab);
     }
-    if (h_status) cudaFreeHost(h_status);
+    if (d_jstat) cudaFree(d_jstat);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (d_tot) cudaFree(d_tot);
@@ -1198,6 +1354,20 @@ int smcrt_plan_status(smcrt_plan *pl, int32_t *status)
     return SMCRT_OK;
 }
 
+int smcrt_plan_set_time_limit(smcrt_plan *pl, double seconds)
+{
+    if (!pl || !(seconds >= 0.0) || !std::isfinite(seconds)) return SMCRT_ERR_BAD_ARG;
+    pl->time_limit_s = seconds;
+    return SMCRT_OK;
+}
+
+int smcrt_set_time_limit(smcrt_ctx *ctx, double seconds)
+{
+    if (!ctx || !(seconds >= 0.0) || !std::isfinite(seconds)) return SMCRT_ERR_BAD_ARG;
+    ctx->time_limit_s = seconds;
+    return SMCRT_OK;
+}
+
 int smcrt_plan_autotune(smcrt_plan *pl, uint64_t trial, int32_t *blocks_out, int32_t *threads_out,
                         int32_t *variant_out)
 {
@@ -1311,7 +1481,8 @@ int smcrt_run(smcrt_ctx *ctx, const smcrt_scene *scene, const smcrt_source *sour
             rc = SMCRT_ERR_CUDA;
     }
     int32_t ks = 0;
-    if (rc == SMCRT_OK && smcrt_plan_status(pl, &ks) == SMCRT_OK && ks) rc = SMCRT_ERR_DEVICE;
+    if (rc == SMCRT_OK && smcrt_plan_status(pl, &ks) == SMCRT_OK && ks)
+        rc = (ks & kStatusTimeout) ? SMCRT_ERR_TIMEOUT : SMCRT_ERR_DEVICE;
     if (rc == SMCRT_OK) *totals_out = t;
     if (dflu && !dev_out) cudaFree(dflu);
     if (dtot) cudaFree(dtot);

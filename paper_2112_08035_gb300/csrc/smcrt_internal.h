@@ -227,11 +227,14 @@ struct JobWork {
     long long park_cycles;        // > 0: park a packet after this many SM cycles in the launch
     int32_t stage;                // mixed kernel: stage the scene tables in shared memory
     int32_t stage_pad;
+    int32_t *jstat;               // device, may be null: this job's own status word (bits OR-ed in)
+    unsigned long long time_limit_ns;   // > 0: a warp stops this job that long after it started on it
 };
 
 // Kernel status word bits.
-constexpr int kStatusBadJob = 1;
+constexpr int kStatusBadJob = SMCRT_STATUS_BAD_JOB;
 constexpr int kStatusStackOverflow = 2;
+constexpr int kStatusTimeout = SMCRT_STATUS_TIMEOUT;
 
 // Launch wrappers, one per translation unit; `variant` selects the register
 // budget of the kernel instantiation (0 .. kNumVariants-1).

@@ -61,6 +61,7 @@ __device__ __forceinline__ void land32(float qx, float qy, float qz, float vx, f
 // atomics to the voxel where a pencil beam enters, which every packet's
 // first tally piece already hits, and serialised there (10 % of the slab's
 // time).
+
 // Length of the approach from a point |dstar| from the surface along a ray
 // with |u.n| = |cdot| (floored at kLandCos, as the landing is).  Explicitly
 // rounded operations here and in cross32's charge: no multiply-add is
@@ -352,7 +353,7 @@ __device__ __forceinline__ void stage_tables(WarpShared *ws, int lane)
 //   5 one Philox call serving launch, interaction and Fresnel draws,
 //   6 the consumers: release a packet, scatter (HG + roulette), Fresnel.
 template <bool G>
-__device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
+__device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
                              int lane)
 {
     const float delta = S.delta32, hstep = S.h32;
@@ -376,6 +377,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
     long long pA = 0, pG = 0;
     uint32_t id_lo = 0, id_hi = 0, event = 0;
     uint32_t t_acq = 0;
+    bool timed_out = false;              // the launch's time limit stopped the refills
 
     for (;;) {
         // ---- 1. refill: this job's parked packets first, then new ids
@@ -421,14 +423,16 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             if (need) {
                 const int leader = __ffs(need) - 1;
                 unsigned long long base = 0;
-                if (lane == leader)
-                    base = (*(volatile int32_t *)&J->cancelled)
-                               ? ~0ull
-                               : atomicAdd(&J->next, (unsigned long long)__popc(need));
+                if (lane == leader) {
+                    if (*(volatile int32_t *)&J->cancelled) base = ~0ull;
+                    else if (SMCRT_RARE(past_deadline(jc))) base = ~0ull - 1u;   // device time limit
+                    else base = atomicAdd(&J->next, (unsigned long long)__popc(need));
+                }
                 base = __shfl_sync(SMCRT_FULL, base, leader);
+                timed_out = timed_out || base == ~0ull - 1u;
                 if (want) {
                     const unsigned long long id = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                    if (base == ~0ull || id >= jc->end) {
+                    if (base >= ~0ull - 1u || id >= jc->end) {
                         retired = true;
                     } else {
                         id_lo = (uint32_t)id;
@@ -698,6 +702,7 @@ __device__ void run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
     }
     const long long pc = warp_sum((long long)npieces);
     if (lane == 0) wadd(wa, kPieces, pc);
+    return timed_out;
 }
 
 template <int kMinBlocks, bool G>
@@ -728,7 +733,10 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
         src = (const DevScene *)__shfl_sync(SMCRT_FULL, (unsigned long long)src, 0);
         if (nxt >= e && !parked) continue;
         if (src == nullptr || J->totals == nullptr) {
-            if (lane == 0) atomicOr(status, kStatusBadJob);
+            if (lane == 0) {
+                atomicOr(status, kStatusBadJob);
+                if (J->jstat != nullptr) atomicOr(J->jstat, kStatusBadJob);
+            }
             continue;
         }
         const long long *s8 = reinterpret_cast<const long long *>(src);
@@ -737,16 +745,26 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
         __syncwarp();
         if (J->stage) stage_tables(ws, lane);
         if (!G && ws->S.general) {           // a scene with general shapes needs the G instantiation
-            if (lane == 0) atomicOr(status, kStatusBadJob);
+            if (lane == 0) {
+                atomicOr(status, kStatusBadJob);
+                if (J->jstat != nullptr) atomicOr(J->jstat, kStatusBadJob);
+            }
             continue;
         }
         if (lane == 0) jobconst_fill(&ws->jc, J);
         wacc_clear(&ws->acc, lane);
         const long long t0 = clock64();
-        run_job_mixed<G>(ws->S, &ws->acc, &ws->jc, J, lane);
+        const bool timed_out = run_job_mixed<G>(ws->S, &ws->acc, &ws->jc, J, lane);
         __syncwarp();
         if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
         wacc_flush(&ws->acc, J->totals, lane);
+        if (timed_out) {                     // the launch's time limit: this warp is done
+            if (lane == 0) {
+                atomicOr(status, kStatusTimeout);
+                if (J->jstat != nullptr) atomicOr(J->jstat, kStatusTimeout);
+            }
+            return;
+        }
     }
 }
 

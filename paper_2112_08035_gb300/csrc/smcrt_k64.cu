@@ -62,7 +62,7 @@ struct WarpShared {
 // the oracle's run of a packet is a sequence of the same IEEE operations on
 // the same values, so its tallies come out bit for bit.
 template <bool G>
-__device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
+__device__ bool run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
                              int lane)
 {
     const double delta = S.delta;
@@ -77,6 +77,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
     long long pA = 0, pG = 0;
     uint32_t id_lo = 0, id_hi = 0, event = 0;
     uint32_t t_acq = 0;
+    bool timed_out = false;              // the launch's time limit stopped the refills
 
     for (;;) {
         // ---- 1. refill: this job's parked packets first, then new ids
@@ -116,14 +117,16 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
             if (need) {
                 const int leader = __ffs(need) - 1;
                 unsigned long long base = 0;
-                if (lane == leader)
-                    base = (*(volatile int32_t *)&J->cancelled)
-                               ? ~0ull
-                               : atomicAdd(&J->next, (unsigned long long)__popc(need));
+                if (lane == leader) {
+                    if (*(volatile int32_t *)&J->cancelled) base = ~0ull;
+                    else if (SMCRT_RARE(past_deadline(jc))) base = ~0ull - 1u;   // device time limit
+                    else base = atomicAdd(&J->next, (unsigned long long)__popc(need));
+                }
                 base = __shfl_sync(SMCRT_FULL, base, leader);
+                timed_out = timed_out || base == ~0ull - 1u;
                 if (want) {
                     const unsigned long long id = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                    if (base == ~0ull || id >= jc->end) {
+                    if (base >= ~0ull - 1u || id >= jc->end) {
                         retired = true;
                     } else {
                         id_lo = (uint32_t)id;
@@ -400,6 +403,7 @@ __device__ void run_job_fp64(const DevScene &S, WarpAcc *wa, const volatile JobC
     }
     const long long pc = warp_sum((long long)npieces);
     if (lane == 0) wadd(wa, kPieces, pc);
+    return timed_out;
 }
 
 template <int kMinBlocks, bool G>
@@ -430,23 +434,36 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_fp64(JobWork *jobs, i
         src = (const DevScene *)__shfl_sync(SMCRT_FULL, (unsigned long long)src, 0);
         if (nxt >= e && !parked) continue;
         if (src == nullptr || J->totals == nullptr) {
-            if (lane == 0) atomicOr(status, kStatusBadJob);
+            if (lane == 0) {
+                atomicOr(status, kStatusBadJob);
+                if (J->jstat != nullptr) atomicOr(J->jstat, kStatusBadJob);
+            }
             continue;
         }
         const long long *s8 = reinterpret_cast<const long long *>(src);
         long long *d8 = reinterpret_cast<long long *>(&ws->S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
         if (!G && ws->S.general) {           // a scene with general shapes needs the G instantiation
-            if (lane == 0) atomicOr(status, kStatusBadJob);
+            if (lane == 0) {
+                atomicOr(status, kStatusBadJob);
+                if (J->jstat != nullptr) atomicOr(J->jstat, kStatusBadJob);
+            }
             continue;
         }
         if (lane == 0) jobconst_fill(&ws->jc, J);
         wacc_clear(&ws->acc, lane);
         const long long t0 = clock64();
-        run_job_fp64<G>(ws->S, &ws->acc, &ws->jc, J, lane);
+        const bool timed_out = run_job_fp64<G>(ws->S, &ws->acc, &ws->jc, J, lane);
         __syncwarp();
         if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
         wacc_flush(&ws->acc, J->totals, lane);
+        if (timed_out) {                     // the launch's time limit: this warp is done
+            if (lane == 0) {
+                atomicOr(status, kStatusTimeout);
+                if (J->jstat != nullptr) atomicOr(J->jstat, kStatusTimeout);
+            }
+            return;
+        }
     }
 }
 

@@ -1302,10 +1302,30 @@ __device__ __forceinline__ void wacc_flush(WarpAcc *a, smcrt_totals *t, int lane
 // packet loop.
 struct JobConst {
     unsigned long long flu, recs, end, begin, dfr;
+    unsigned long long deadline;   // global timer (ns) after which the warp stops the job (0 = never)
     uint32_t k0, k1;
     int32_t din;
     uint32_t budget;          // park after this many clock() cycles (0 = never)
 };
+
+// The GPU's global nanosecond timer (the same clock on every SM).
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device-side time limit of a launch, checked where a warp claims new
+// packet ids (no cost in the packet loop itself): past the job's deadline
+// the warp claims no more ids, the packets it holds finish as usual (each
+// bounded by the step cap), and the warp returns.  The totals and the
+// fluence then cover exactly the packets counted.
+__device__ __forceinline__ bool past_deadline(const volatile JobConst *jc)
+{
+    const unsigned long long dl = jc->deadline;
+    return dl != 0ull && globaltimer_ns() > dl;
+}
 
 __device__ __forceinline__ void jobconst_fill(volatile JobConst *jc, const JobWork *J)
 {
@@ -1319,6 +1339,7 @@ __device__ __forceinline__ void jobconst_fill(volatile JobConst *jc, const JobWo
     jc->din = J->defer_in & 1;
     const long long b = J->defer != nullptr ? J->park_cycles : 0;
     jc->budget = (uint32_t)(b > 0x7fffffffLL ? 0x7fffffffLL : (b < 0 ? 0 : b));
+    jc->deadline = J->time_limit_ns > 0ull ? globaltimer_ns() + J->time_limit_ns : 0ull;
 }
 
 enum Phase { kTrace = 0, kNrm = 1, kProj = 2, kFar = 3, kNear = 4, kLaunch = 5 };

@@ -132,3 +132,50 @@ def test_scheduler_setup_failure_fails_jobs_cleanly():
     assert f"wait error {smc.ERR_NO_MEMORY}" in lines, r.stdout
     assert f"submit error {smc.ERR_NO_MEMORY}" in lines, r.stdout
     assert "closed" in lines, r.stdout
+
+
+_BAD_JOB_CHILD = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import paper_2112_08035_gb300 as smc
+import workloads as W
+ctx = smc.Context(0)
+good = W.sphere_pencil(20_000, 31, "mixed")
+fa, ta = ctx.run(good, "mixed")
+bad_id = ctx.submit(W.three_layer_slab(50_000, 32, "mixed", grid_n=20))   # job 1: no scene in the round table
+good_id = ctx.submit(good)                                                  # job 2, in the same rounds
+for name, jid in (("bad", bad_id), ("good", good_id)):
+    try:
+        f, t, _ = ctx.wait(jid, 120.0)
+        same = bool(np.array_equal(f, fa) and t["A"] == ta["A"] and t["packets"] == good.npackets)
+        print(name, "ok", same)
+    except smc.SmcrtError as e:
+        print(name, "error", e.code)
+# a later job on the same server
+f, t, _ = ctx.wait(ctx.submit(good), 120.0)
+print("later ok", bool(np.array_equal(f, fa)))
+ctx.close()
+print("closed")
+"""
+
+
+def test_bad_job_fails_alone():
+    # a job the kernel flags (its round-table entry carries no scene, injected
+    # on the host) fails with SMCRT_ERR_DEVICE; the good job in the same
+    # rounds, and a later one, complete normally with their exact results:
+    # each job has its own status word and the round's word is cleared
+    # before every round (no GPU fault is involved)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SMCRT_FAULT_BAD_JOB="1")
+    r = subprocess.run([sys.executable, "-c", _BAD_JOB_CHILD, root], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.split("\n")
+    assert f"bad error {smc.ERR_DEVICE}" in lines, r.stdout
+    assert "good ok True" in lines, r.stdout
+    assert "later ok True" in lines, r.stdout
+    assert "closed" in lines, r.stdout
