@@ -709,6 +709,7 @@ constexpr int kMaxSlots = 64;
 constexpr int kRoundsInFlight = 2;
 constexpr double kRoundSeconds = 0.008;   // target device time of one round
 constexpr double kParkSeconds = 0.004;    // device time a packet may run per round before it is parked
+constexpr double kDrainSeconds = 0.0005;  // ... once its warp has no more work, in rounds with new ids
 constexpr unsigned kDeferCap = 65536;     // parked packets per list and job
 
 size_t job_bytes(const smcrt_grid &g)
@@ -790,12 +791,13 @@ void scheduler(smcrt_ctx *ctx)
     if (d_jstat) chk(cudaMemset(d_jstat, 0, sizeof(int32_t) * kMaxSlots), SMCRT_ERR_CUDA);
     chk(cudaMalloc(&d_tot, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_NO_MEMORY);
     if (d_tot) chk(cudaMemset(d_tot, 0, sizeof(smcrt_totals) * kMaxSlots), SMCRT_ERR_CUDA);
-    // Launch shape of the served kernels.  The mixed kernel's register
-    // variant, scene-table staging, threads and blocks are chosen by timing
-    // trials on the first mixed job served (tune_served below) before the
-    // graphs are captured; until then, and for FP64, the defaults.
-    int threads_m = 128, variant_m = default_variant(SMCRT_MIXED), stage_m = 1;
-    int blocks_m = ctx->sm_count * std::max(1, occupancy_mixed(threads_m, variant_m));
+    // Launch shape of the served kernels.  The mixed jobs run in the kernel
+    // whose warps hold two jobs at a time (launch_mixed_multi); its register
+    // variant, threads and blocks are chosen by timing trials on the first
+    // mixed job served (tune_served below) before the graphs are captured;
+    // until then, and for FP64, the defaults.
+    int threads_m = 128, variant_m = 0;
+    int blocks_m = ctx->sm_count * std::max(1, occupancy_mixed_multi(threads_m, variant_m));
     const int threads_d = 128;
     const int blocks_d = ctx->sm_count * std::max(1, occupancy_fp64(threads_d, default_variant(SMCRT_FP64)));
     bool tuned_served = false;
@@ -804,6 +806,7 @@ void scheduler(smcrt_ctx *ctx)
     // warp-cycles one round can spend (the mixed kernel's resident warps)
     auto round_cycles = [&] { return (double)blocks_m * (threads_m / 32) * clk_khz * 1e3 * kRoundSeconds; };
     const long long park_cycles = (long long)(clk_khz * 1e3 * kParkSeconds);
+    const long long drain_cycles = (long long)(clk_khz * 1e3 * kDrainSeconds);
     // SMCRT_FAULT_BAD_JOB=<job id>: that job's round-table entry gets no
     // scene, which the kernels report as a bad job (host-side injection for
     // the status tests; no GPU fault is involved).
@@ -850,7 +853,7 @@ void scheduler(smcrt_ctx *ctx)
                 launch_round_prologue(b.d_tab, 2 * kMaxSlots, st);
                 cudaEventRecord(ev_fork, st);
                 cudaStreamWaitEvent(st2, ev_fork, 0);
-                launch_mixed(b.d_tab, kMaxSlots, d_status + bi, blocks_m, threads_m, st, variant_m + off);
+                launch_mixed_multi(b.d_tab, kMaxSlots, d_status + bi, blocks_m, threads_m, st, variant_m + off);
                 launch_fp64(b.d_tab + kMaxSlots, kMaxSlots, d_status + bi, blocks_d, threads_d, st2,
                             default_variant(SMCRT_FP64) + off);
                 cudaEventRecord(ev_join, st2);
@@ -872,10 +875,9 @@ void scheduler(smcrt_ctx *ctx)
     if (setup_rc == SMCRT_OK) setup_rc = capture();
 
     // Timing trials of the served mixed kernel on one job's scene (scratch
-    // tallies, ids from 0 with the job's seed): register variant x scene
-    // tables in global or shared memory x threads x resident blocks, as
-    // smcrt_plan_autotune does for a plan.  Results do not depend on the
-    // choice (every variant computes the same bits).
+    // tallies, ids from 0 with the job's seed): register variant x threads x
+    // resident blocks, as smcrt_plan_autotune does for a plan.  Results do
+    // not depend on the choice (every variant computes the same bits).
     auto tune_served = [&](const Job &j) {
         const uint64_t trial = std::min<uint64_t>(j.npackets, 50000);
         const size_t cells = (size_t)j.grid.n[0] * j.grid.n[1] * j.grid.n[2];
@@ -888,10 +890,9 @@ void scheduler(smcrt_ctx *ctx)
                   cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
         const int off = j.plan->host.general ? kNumVariants : 0;
         float best = 1e30f;
-        for (int pv = 0; ok && pv < 2 * kNumVariants; ++pv) {
-            const int v = pv % kNumVariants, stage = pv / kNumVariants;
+        for (int v = 0; ok && v < 2; ++v) {
             for (int t : {64, 128}) {
-                const int occ = occupancy_mixed(t, v + off);
+                const int occ = occupancy_mixed_multi(t, v + off);
                 if (occ < 1) continue;
                 for (int mult : {1, 2}) {
                     const int b = ctx->sm_count * occ * mult;
@@ -903,12 +904,11 @@ void scheduler(smcrt_ctx *ctx)
                     w.fluence = (long long *)flu;
                     w.totals = (smcrt_totals *)tot;
                     w.scene = j.plan->dscene;
-                    w.stage = stage;
                     cudaMemsetAsync(flu, 0, cells * 8, st);
                     cudaMemsetAsync(tot, 0, sizeof(smcrt_totals), st);
                     if (launch_set_job((JobWork *)tab, w, st) != cudaSuccess) { ok = false; break; }
                     cudaEventRecord(e0, st);
-                    if (launch_mixed((JobWork *)tab, 1, (int *)tst, b, t, st, v + off) != cudaSuccess) {
+                    if (launch_mixed_multi((JobWork *)tab, 1, (int *)tst, b, t, st, v + off) != cudaSuccess) {
                         ok = false;
                         break;
                     }
@@ -919,7 +919,6 @@ void scheduler(smcrt_ctx *ctx)
                     if (ms < best) {
                         best = ms;
                         variant_m = v;
-                        stage_m = stage;
                         threads_m = t;
                         blocks_m = b;
                     }
@@ -935,8 +934,8 @@ void scheduler(smcrt_ctx *ctx)
         if (e1) cudaEventDestroy(e1);
         cudaGetLastError();
         if (trace)
-            std::fprintf(stderr, "[smcrt] served kernel tuned on job %llu: variant %d stage %d threads %d blocks %d\n",
-                         (unsigned long long)j.id, variant_m, stage_m, threads_m, blocks_m);
+            std::fprintf(stderr, "[smcrt] served kernel tuned on job %llu: variant %d threads %d blocks %d\n",
+                         (unsigned long long)j.id, variant_m, threads_m, blocks_m);
         return ok;
     };
 
@@ -1106,10 +1105,9 @@ void scheduler(smcrt_ctx *ctx)
                     const int rc = capture();
                     if (rc != SMCRT_OK) {
                         // keep serving with the default shape captured at set-up
-                        variant_m = default_variant(SMCRT_MIXED);
+                        variant_m = 0;
                         threads_m = 128;
-                        stage_m = 1;
-                        blocks_m = ctx->sm_count * std::max(1, occupancy_mixed(threads_m, variant_m));
+                        blocks_m = ctx->sm_count * std::max(1, occupancy_mixed_multi(threads_m, variant_m));
                         if (capture() != SMCRT_OK) {
                             for (auto &j : active) complete(j, nullptr, SMCRT_ERR_CUDA);
                             active.clear();
@@ -1149,10 +1147,13 @@ void scheduler(smcrt_ctx *ctx)
             w.scene = j->id == bad_job ? nullptr : j->plan->dscene;
             w.cancelled = 0;
             w.park_cycles = park_cycles;
+            // a round with new ids ends soon after they run out; a round of
+            // parked packets only lets them run the full budget
+            w.drain_cycles = nfresh > 0 ? drain_cycles : park_cycles;
             w.jstat = d_jstat + j->slot;
             w.defer = j->ddefer;
             w.defer_in = (int32_t)(issued & 1);
-            w.stage = j->precision == SMCRT_MIXED ? stage_m : 0;
+            w.stage = 0;   // the served kernels read the scene tables from global memory
             j->cursor += q;
             j->last_round = issued;
             if (j->precision == SMCRT_FP64) B.h_tab[kMaxSlots + nd++] = w;

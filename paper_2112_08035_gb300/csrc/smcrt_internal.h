@@ -225,6 +225,8 @@ struct JobWork {
     int32_t defer_in;             // list resumed in this launch (0 / 1)
     JobDefer *defer;              // device, may be null (no parking)
     long long park_cycles;        // > 0: park a packet after this many SM cycles in the launch
+    long long drain_cycles;       // > 0 (served rounds): once its warp finds no job with work left,
+                                  // park a packet after this many SM cycles in the launch
     int32_t stage;                // mixed kernel: stage the scene tables in shared memory
     int32_t stage_pad;
     int32_t *jstat;               // device, may be null: this job's own status word (bits OR-ed in)
@@ -245,6 +247,12 @@ cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int 
                          cudaStream_t stream, int variant = 0);
 int occupancy_fp64(int threads, int variant = 0);
 int occupancy_mixed(int threads, int variant = 0);
+// Served rounds' mixed kernel, whose warps hold two jobs at a time (lanes
+// refill from the next job instead of draining each): variant 0 / 1 = 5 / 4
+// resident blocks of 128 threads, + kNumVariants for general shapes.
+cudaError_t launch_mixed_multi(JobWork *jobs, int njobs, int *status, int blocks, int threads,
+                               cudaStream_t stream, int variant = 0);
+int occupancy_mixed_multi(int threads, int variant = 0);
 cudaError_t launch_set_job(JobWork *dst, const JobWork &v, cudaStream_t stream);
 // Field validation of scene / source / grid, without compiling or
 // allocating (host runtime).

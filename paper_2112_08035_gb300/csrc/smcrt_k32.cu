@@ -305,16 +305,29 @@ static __device__ __noinline__ Launched launch32(const DevScene &S, uint4 r)
 // the instruction stream, primitive kinds, FP32 primitive and region tables
 // and region ranges of its job into shared memory when they fit here.
 constexpr int kStageBytes = 4096;
-struct WarpShared {
+// One job as a warp holds it: its scene, its tally accumulator, its constants.
+struct JobSlot {
     DevScene S;
     WarpAcc acc;
     JobConst jc;
+};
+struct WarpShared {          // plan launches: one job at a time, tables optionally staged
+    JobSlot slot;
     __align__(16) unsigned char tab[kStageBytes];
+};
+// Served rounds: two jobs at a time.  A warp's lanes carry packets of either
+// job; the warp feeds new packets from one slot and, when that job runs out
+// of ids, stages the next job with work into the other slot as soon as no
+// lane holds a packet there -- lanes refill from the next job instead of
+// the warp draining each job it visits.  Tables are read from global memory.
+constexpr int kMultiSlots = 2;
+struct WarpSharedMulti {
+    JobSlot slot[kMultiSlots];
 };
 
 __device__ __forceinline__ void stage_tables(WarpShared *ws, int lane)
 {
-    DevScene &SS = ws->S;
+    DevScene &SS = ws->slot.S;
     const int ni = SS.ninstr, np = SS.nprims, nr = SS.nregions;
     const int w_ins = 4 * ni, w_kind = np, w_p32 = 8 * np, w_r32 = 8 * nr, w_rr = 2 * nr;   // 4-byte words
     const int o1 = 0, o2 = o1 + ((w_ins + 3) & ~3), o3 = o2 + ((w_kind + 3) & ~3), o4 = o3 + ((w_p32 + 3) & ~3),
@@ -342,6 +355,69 @@ __device__ __forceinline__ void stage_tables(WarpShared *ws, int lane)
     __syncwarp();
 }
 
+// Served rounds: the first job of jobs[start, ...) (cyclically) with work
+// for a warp -- new ids or parked packets -- other than `exclude`; -1 if
+// none.  The lanes look at 32 entries at a time.  A descriptor without
+// scene or totals, or a scene that needs the general-shape kernel in the
+// plain one, is flagged in the launch's and the job's status words and
+// skipped from then on.  Warp-collective; the result is warp-uniform.
+template <bool G>
+__device__ int multi_find(JobWork *jobs, int njobs, int start, int exclude, unsigned long long &skip, int *status,
+                          int lane)
+{
+    for (int b = 0; b < njobs; b += 32) {
+        const int k = b + lane;
+        int j = start + k;
+        if (j >= njobs) j -= njobs;
+        bool work = false, bad = false;
+        if (k < njobs && j != exclude && !((skip >> j) & 1ull)) {
+            JobWork *J = jobs + j;
+            const unsigned long long nxt = *(volatile unsigned long long *)&J->next;
+            bool parked = false;
+            if (J->defer != nullptr) {
+                const int in = J->defer_in & 1;
+                parked = min(*(volatile unsigned *)&J->defer->count[in], J->defer->cap) >
+                         *(volatile unsigned *)&J->defer->cursor[in];
+            }
+            // a cancelled job's ids are no work (its parked packets still are)
+            const bool fresh = nxt < J->end && *(volatile int32_t *)&J->cancelled == 0;
+            if (fresh || parked) {
+                if (J->scene == nullptr || J->totals == nullptr || (!G && J->scene->general)) {
+                    bad = true;
+                    atomicOr(status, kStatusBadJob);
+                    if (J->jstat != nullptr) atomicOr(J->jstat, kStatusBadJob);
+                } else {
+                    work = true;
+                }
+            }
+        }
+        // bad jobs are skipped by this warp from now on (warp-uniform mask)
+        for (unsigned m = __ballot_sync(SMCRT_FULL, bad); m != 0u; m &= m - 1u) {
+            int jb = start + b + (__ffs(m) - 1);
+            if (jb >= njobs) jb -= njobs;
+            skip |= 1ull << jb;
+        }
+        const unsigned hit = __ballot_sync(SMCRT_FULL, work);
+        if (hit != 0u) {
+            const int j0 = start + b + (__ffs(hit) - 1);
+            return j0 >= njobs ? j0 - njobs : j0;
+        }
+    }
+    return -1;
+}
+
+// Served rounds: stage job J into a slot (scene header copied from global
+// memory, constants, zeroed accumulator).  Warp-collective.
+__device__ __forceinline__ void multi_stage(JobSlot *sl, JobWork *J, int lane)
+{
+    const long long *s8 = reinterpret_cast<const long long *>(J->scene);
+    long long *d8 = reinterpret_cast<long long *>(&sl->S);
+    for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
+    if (lane == 0) jobconst_fill(&sl->jc, J);
+    wacc_clear(&sl->acc, lane);
+    __syncwarp();
+}
+
 // One warp works through packet ids of job J until the job's cursor passes
 // its end.  Iteration structure (all lanes execute every stage; a lane's
 // phase only selects operands or predicates a short update):
@@ -352,11 +428,36 @@ __device__ __forceinline__ void stage_tables(WarpShared *ws, int lane)
 //   4 the track-length tally of this iteration's move (one call site),
 //   5 one Philox call serving launch, interaction and Fresnel draws,
 //   6 the consumers: release a packet, scatter (HG + roulette), Fresnel.
-template <bool G>
-__device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile JobConst *jc, JobWork *J,
-                             int lane)
+//
+// MULTI = false (plan launches): one job, jobs[0], in slots[0].  MULTI =
+// true (served rounds): the warp works through the table jobs[0, njobs)
+// starting at `first`, holding up to two jobs in slots[0..1] (see
+// WarpSharedMulti); each lane's packet belongs to the job of its slot js.
+template <bool G, bool MULTI>
+__device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int first, int *status, int lane)
 {
-    const float delta = S.delta32, hstep = S.h32;
+    const DevScene &S0 = slots[0].S;
+    const float delta0 = S0.delta32, hstep0 = S0.h32;
+    const volatile JobConst *const jc0 = &slots[0].jc;
+    JobWork *const J = jobs;
+    int js = 0;                          // the lane's job slot
+    // served rounds (warp-uniform): the slot fed with new packets, the job of
+    // each slot (-1: none), the next table entry to look at, and the jobs
+    // this warp found unusable (a descriptor without scene or totals)
+    int feed = 0, sj0 = -1, sj1 = -1, scan = first;
+    unsigned long long skip = 0ull;
+    // served rounds: no job had work left when this warp last looked.  Its
+    // packets then park sooner (after the round's drain budget instead of the
+    // full one), so a round is not held open by a few long-lived packets
+    // while the rest of the GPU idles; they resume next round among new work.
+    bool drained = false;
+    if (MULTI) {
+        const int nj = multi_find<G>(jobs, njobs, scan, -1, skip, status, lane);
+        if (nj < 0) return false;
+        multi_stage(slots, jobs + nj, lane);
+        sj0 = nj;
+        scan = nj + 1 < njobs ? nj + 1 : 0;
+    }
 
     bool alive = false, retired = false;
     float px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0, w = 0, tau = 0;
@@ -381,8 +482,93 @@ __device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
 
     for (;;) {
         // ---- 1. refill: this job's parked packets first, then new ids
-        {
+        if (MULTI) {
             unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            for (int pass = 0; need != 0u && pass < 4; ++pass) {
+                JobSlot *const sf = slots + feed;
+                JobWork *const Jf = jobs + (feed ? sj1 : sj0);
+                JobDefer *const dfr = (JobDefer *)sf->jc.dfr;
+                if (dfr != nullptr) {          // the feed job's parked packets
+                    const int din = sf->jc.din;
+                    const int leader = __ffs(need) - 1;
+                    unsigned base = 0u, avail = 0u;
+                    if (lane == leader) {
+                        avail = min(*(volatile unsigned *)&dfr->count[din], dfr->cap);
+                        base = atomicAdd(&dfr->cursor[din], (unsigned)__popc(need));
+                    }
+                    base = __shfl_sync(SMCRT_FULL, base, leader);
+                    avail = __shfl_sync(SMCRT_FULL, avail, leader);
+                    if (!alive && !retired) {
+                        const unsigned k = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+                        if (k < avail) {
+                            const DeferState &d = dfr->buf[din][k];
+                            px = (float)d.p[0]; py = (float)d.p[1]; pz = (float)d.p[2];
+                            ux = (float)d.u[0]; uy = (float)d.u[1]; uz = (float)d.u[2];
+                            w = (float)d.w; tau = (float)d.tau;
+                            pA = d.pA; pG = d.pG;
+                            id_lo = d.id_lo; id_hi = d.id_hi; event = d.event;
+                            nsteps = (int)d.nsteps; pscat = d.pscat;
+                            phase = kTrace;
+                            cs = __uint_as_float(d.pad[0]);
+                            pend = __uint_as_float(d.pad[1]);
+                            if (cs >= 0.f) {
+                                qx = px; qy = py; qz = pz;
+                                px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
+                            }
+                            t_acq = (uint32_t)clock();
+                            alive = true;
+                            js = feed;
+                        }
+                    }
+                    need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+                }
+                if (need != 0u) {              // the feed job's new ids
+                    const int leader = __ffs(need) - 1;
+                    unsigned long long base = 0;
+                    if (lane == leader)
+                        base = *(volatile int32_t *)&Jf->cancelled
+                                   ? ~0ull
+                                   : atomicAdd(&Jf->next, (unsigned long long)__popc(need));
+                    base = __shfl_sync(SMCRT_FULL, base, leader);
+                    if (!alive && !retired) {
+                        const unsigned long long id =
+                            base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+                        if (base != ~0ull && id < sf->jc.end) {
+                            id_lo = (uint32_t)id;
+                            id_hi = (uint32_t)(id >> 32);
+                            event = 0u;
+                            phase = kLaunch;
+                            t_acq = (uint32_t)clock();
+                            alive = true;
+                            js = feed;
+                        }
+                    }
+                    need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+                }
+                if (need == 0u) break;
+                // the feed job has no work left for these lanes: feed the
+                // other slot with the next job that has some, once no lane
+                // holds a packet there
+                const int o = 1 - feed;
+                if (__ballot_sync(SMCRT_FULL, alive && js == o) != 0u) break;
+                const int oj = o ? sj1 : sj0;
+                if (oj >= 0) wacc_flush(&slots[o].acc, jobs[oj].totals, lane);
+                const int nj = multi_find<G>(jobs, njobs, scan, feed ? sj1 : sj0, skip, status, lane);
+                if (o) sj1 = -1; else sj0 = -1;
+                if (nj < 0) {                  // no job has work left: idle lanes retire
+                    if (!alive) retired = true;
+                    drained = true;
+                    break;
+                }
+                multi_stage(slots + o, jobs + nj, lane);
+                if (o) sj1 = nj; else sj0 = nj;
+                scan = nj + 1 < njobs ? nj + 1 : 0;
+                feed = o;
+            }
+            if (__all_sync(SMCRT_FULL, retired)) break;
+        } else {
+            unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            const volatile JobConst *const jc = jc0;
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
             if (SMCRT_RARE(need && dfr != nullptr)) {
@@ -447,6 +633,13 @@ __device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             if (__all_sync(SMCRT_FULL, retired)) break;
         }
 
+        // the lane's job: its scene, constants and accumulator (one job in a
+        // plan launch; compile-time slot 0 there)
+        const DevScene &S = MULTI ? slots[js].S : S0;
+        const float delta = MULTI ? S.delta32 : delta0, hstep = MULTI ? S.h32 : hstep0;
+        const volatile JobConst *const jc = MULTI ? &slots[js].jc : jc0;
+        WarpAcc *const wa = MULTI ? &slots[js].acc : &slots[0].acc;
+
         // ---- 2. the scene evaluation of this iteration
         const float sg = cdot > 0.f ? 1.f : -1.f;
         float ex = px, ey = py, ez = pz;
@@ -461,7 +654,12 @@ __device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             ex = qx + e * nx; ey = qy + e * ny; ez = qz + e * nz;
         }
         const Eval32 E = scene_eval32<G>(S, ex, ey, ez, sel);
-        {
+        if (MULTI) {                           // evaluations counted per job slot
+            for (int k = 0; k < kMultiSlots; ++k) {
+                const unsigned ev = __ballot_sync(SMCRT_FULL, alive && phase != kLaunch && js == k);
+                if (lane == 0 && ev != 0u) wadd(&slots[k].acc, kEvals, __popc(ev));
+            }
+        } else {
             const unsigned ev = __ballot_sync(SMCRT_FULL, alive && phase != kLaunch);
             if (lane == 0) wadd(wa, kEvals, __popc(ev));
         }
@@ -665,6 +863,11 @@ __device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
             wadd(wa, kR, fin_R); wadd(wa, kT, fin_T); wadd(wa, kKilled, fin_K);
             wadd(wa, kA, pA); wadd(wa, kGain, pG); wadd(wa, kScat, pscat); wadd(wa, kSteps, nsteps);
             wadd(wa, kPackets, 1);
+            if (MULTI) {                       // a lane's pieces and time go to its packet's job
+                wadd(wa, kPieces, npieces);
+                npieces = 0u;
+                wadd(wa, kBusy, (long long)(((uint32_t)clock() - t_acq) >> 5));
+            }
             smcrt_packet_record *const recs = (smcrt_packet_record *)jc->recs;
             if (recs) {
                 smcrt_packet_record r;
@@ -677,7 +880,8 @@ __device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
         // ---- park a straggler at a trace boundary (serving rounds only).  A
         // packet in a crawl is parked as its anchor and crawl length, from
         // which the resume recomputes the same position.
-        if (SMCRT_RARE(alive && phase == kTrace && jc->budget > 0u && (uint32_t)clock() - t_acq > jc->budget)) {
+        if (SMCRT_RARE(alive && phase == kTrace && jc->budget > 0u &&
+                       (uint32_t)clock() - t_acq > (MULTI && drained ? jc->drain : jc->budget))) {
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
             const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);
@@ -693,15 +897,29 @@ __device__ bool run_job_mixed(const DevScene &S, WarpAcc *wa, const volatile Job
                 d.id_lo = id_lo; d.id_hi = id_hi; d.event = event;
                 d.nsteps = (uint32_t)nsteps; d.pscat = pscat;
                 wadd(wa, kParked, 1);
+                if (MULTI) {
+                    wadd(wa, kPieces, npieces);
+                    npieces = 0u;
+                    wadd(wa, kBusy, (long long)(((uint32_t)clock() - t_acq) >> 5));
+                }
                 alive = false;
             } else {
+                // list full: run on and try again after another budget (the
+                // time so far is the job's busy time, as a parked segment's is)
                 atomicAdd(&dfr->overflow, 1u);
-                t_acq = (uint32_t)clock() + 0x7fffffffu;   // list full: run on (one retry per ~1 s)
+                if (MULTI) wadd(wa, kBusy, (long long)(((uint32_t)clock() - t_acq) >> 5));
+                t_acq = (uint32_t)clock();
             }
         }
     }
+    if (MULTI) {                               // the jobs still in the slots
+        __syncwarp();
+        if (sj0 >= 0) wacc_flush(&slots[0].acc, jobs[sj0].totals, lane);
+        if (sj1 >= 0) wacc_flush(&slots[1].acc, jobs[sj1].totals, lane);
+        return false;
+    }
     const long long pc = warp_sum((long long)npieces);
-    if (lane == 0) wadd(wa, kPieces, pc);
+    if (lane == 0) wadd(&slots[0].acc, kPieces, pc);
     return timed_out;
 }
 
@@ -740,24 +958,24 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
             continue;
         }
         const long long *s8 = reinterpret_cast<const long long *>(src);
-        long long *d8 = reinterpret_cast<long long *>(&ws->S);
+        long long *d8 = reinterpret_cast<long long *>(&ws->slot.S);
         for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
         __syncwarp();
         if (J->stage) stage_tables(ws, lane);
-        if (!G && ws->S.general) {           // a scene with general shapes needs the G instantiation
+        if (!G && ws->slot.S.general) {      // a scene with general shapes needs the G instantiation
             if (lane == 0) {
                 atomicOr(status, kStatusBadJob);
                 if (J->jstat != nullptr) atomicOr(J->jstat, kStatusBadJob);
             }
             continue;
         }
-        if (lane == 0) jobconst_fill(&ws->jc, J);
-        wacc_clear(&ws->acc, lane);
+        if (lane == 0) jobconst_fill(&ws->slot.jc, J);
+        wacc_clear(&ws->slot.acc, lane);
         const long long t0 = clock64();
-        const bool timed_out = run_job_mixed<G>(ws->S, &ws->acc, &ws->jc, J, lane);
+        const bool timed_out = run_job_mixed<G, false>(&ws->slot, J, 1, 0, status, lane);
         __syncwarp();
-        if (lane == 0) wadd(&ws->acc, kBusy, clock64() - t0);
-        wacc_flush(&ws->acc, J->totals, lane);
+        if (lane == 0) wadd(&ws->slot.acc, kBusy, clock64() - t0);
+        wacc_flush(&ws->slot.acc, J->totals, lane);
         if (timed_out) {                     // the launch's time limit: this warp is done
             if (lane == 0) {
                 atomicOr(status, kStatusTimeout);
@@ -766,6 +984,20 @@ __global__ void __launch_bounds__(128, kMinBlocks) packets_mixed(JobWork *jobs, 
             return;
         }
     }
+}
+
+// Served rounds: every warp works through the whole job table, two jobs at a
+// time (run_job_mixed<G, true>), starting at a job of its own so that the
+// warps spread over the table.
+template <int kMinBlocks, bool G>
+__global__ void __launch_bounds__(128, kMinBlocks) packets_mixed_multi(JobWork *jobs, int njobs, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    WarpSharedMulti *ws = reinterpret_cast<WarpSharedMulti *>(smem) + warp;
+    if (njobs <= 0) return;
+    run_job_mixed<G, true>(ws->slot, jobs, njobs, gw % njobs, status, lane);
 }
 
 }  // namespace
@@ -790,6 +1022,34 @@ cudaError_t launch_mixed(JobWork *jobs, int njobs, int *status, int blocks, int 
     default: packets_mixed<5, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
     }
     return cudaGetLastError();
+}
+
+// The served kernel: variant 0 / 1 = 5 / 4 resident blocks, plain shapes;
+// 3 / 4 = the same for general shapes (the index space of launch_mixed).
+cudaError_t launch_mixed_multi(JobWork *jobs, int njobs, int *status, int blocks, int threads, cudaStream_t stream,
+                               int variant)
+{
+    const size_t sm = (size_t)(threads / 32) * sizeof(WarpSharedMulti);
+    switch (variant) {
+    case 1: packets_mixed_multi<4, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 3: packets_mixed_multi<5, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    case 4: packets_mixed_multi<4, true><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    default: packets_mixed_multi<5, false><<<blocks, threads, sm, stream>>>(jobs, njobs, status); break;
+    }
+    return cudaGetLastError();
+}
+
+int occupancy_mixed_multi(int threads, int variant)
+{
+    int n = 0;
+    const size_t sm = (size_t)(threads / 32) * sizeof(WarpSharedMulti);
+    switch (variant) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed_multi<4, false>, threads, sm); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed_multi<5, true>, threads, sm); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed_multi<4, true>, threads, sm); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, packets_mixed_multi<5, false>, threads, sm); break;
+    }
+    return n;
 }
 
 int occupancy_mixed(int threads, int variant)

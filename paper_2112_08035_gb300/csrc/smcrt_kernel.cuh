@@ -1306,6 +1306,7 @@ struct JobConst {
     uint32_t k0, k1;
     int32_t din;
     uint32_t budget;          // park after this many clock() cycles (0 = never)
+    uint32_t drain;           // ... or after this many once the warp has no more work (0 = budget)
 };
 
 // The GPU's global nanosecond timer (the same clock on every SM).
@@ -1339,6 +1340,8 @@ __device__ __forceinline__ void jobconst_fill(volatile JobConst *jc, const JobWo
     jc->din = J->defer_in & 1;
     const long long b = J->defer != nullptr ? J->park_cycles : 0;
     jc->budget = (uint32_t)(b > 0x7fffffffLL ? 0x7fffffffLL : (b < 0 ? 0 : b));
+    const long long dr = J->defer != nullptr && J->drain_cycles > 0 ? J->drain_cycles : b;
+    jc->drain = (uint32_t)(dr > 0x7fffffffLL ? 0x7fffffffLL : (dr < 0 ? 0 : dr));
     jc->deadline = J->time_limit_ns > 0ull ? globaltimer_ns() + J->time_limit_ns : 0ull;
 }
 
