@@ -51,7 +51,9 @@ FX = 2.0 ** 32
 #   normalisation 8, roulette 2, log 4 = 62;  interface (normal from the
 #   gradient, Fresnel / Snell cosines and directions) 30;
 #   segment-stepping bound, per move that used it: the bounding box's ray
-#   exit 30, plus per primitive ray bound sphere 15, box 30, capsule 60.
+#   exit 30, each primitive distance it takes (the SDF figures above), and
+#   per primitive ray bound sphere 15, box 30, capsule 60, cylinder 40,
+#   torus 75 (two cylinder intervals and a slab).
 FLOPS_PRIM = {"sphere": 8, "box": 20, "capsule": 22, "torus": 12, "cylinder": 14}
 FLOPS_SMOOTH = 8
 FLOPS_BBOX = 20
@@ -61,7 +63,7 @@ FLOPS_PIECE = 16
 FLOPS_INTERACTION = 62
 FLOPS_INTERFACE = 30
 FLOPS_SEG_BBOX = 30
-FLOPS_SEG_PRIM = {"sphere": 15, "box": 30, "capsule": 60, "torus": 0, "cylinder": 0}
+FLOPS_SEG_PRIM = {"sphere": 15, "box": 30, "capsule": 60, "torus": 75, "cylinder": 40}
 
 
 def algorithmic_work(t: dict, nregions: int) -> dict:
@@ -70,7 +72,8 @@ def algorithmic_work(t: dict, nregions: int) -> dict:
     n = max(1, t["packets"])
     prim = sum(t[f"prim_{k}"] * w for k, w in FLOPS_PRIM.items())
     seg_per_call = FLOPS_SEG_BBOX + (sum(t[f"seg_{k}"] * w for k, w in FLOPS_SEG_PRIM.items())
-                                     / max(1, t["seg_calls"]))
+                                     + sum(t[f"seg_dist_{k}"] * w for k, w in FLOPS_PRIM.items())
+                                     ) / max(1, t["seg_calls"])
     flops = (prim + t["smooth_ops"] * FLOPS_SMOOTH + t["scene_evals"] * (FLOPS_BBOX + FLOPS_REGION * nregions)
              + t["steps"] * FLOPS_STEP + t["pieces"] * FLOPS_PIECE + t["scatters"] * FLOPS_INTERACTION
              + t["interfaces"] * FLOPS_INTERFACE + t["seg_moves"] * seg_per_call)

@@ -74,7 +74,8 @@ class OrGrid(C.Structure):
 TOTAL_FIELDS = ["R", "T", "A", "killed", "gain", "packets", "scatters", "steps", "scene_evals",
                 "prog_evals", "prim_evals", "interfaces", "fresnel", "pieces", "max_steps_hit",
                 "prim_sphere", "prim_box", "prim_capsule", "prim_torus", "prim_cylinder", "smooth_ops",
-                "seg_calls", "seg_sphere", "seg_box", "seg_capsule", "seg_torus", "seg_cylinder", "seg_moves"]
+                "seg_calls", "seg_sphere", "seg_box", "seg_capsule", "seg_torus", "seg_cylinder", "seg_moves",
+                "seg_dist_sphere", "seg_dist_box", "seg_dist_capsule", "seg_dist_torus", "seg_dist_cylinder"]
 
 
 class OrTotals(C.Structure):

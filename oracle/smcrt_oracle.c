@@ -82,6 +82,7 @@ typedef struct {
      * taken in them by kind */
     int64_t prim_kind[5], smooth_ops, seg_calls, seg_kind[5];
     int64_t seg_moves;    /* segment-stepping moves that did not end in an interaction */
+    int64_t seg_dist[5];  /* primitive distances taken by the bounds, by kind */
 } or_totals;
 typedef struct { int64_t R, T, A, killed, gain, scatters, steps, pad; } or_packet;
 
@@ -352,21 +353,26 @@ static double bbox_sdf(const or_scene *S, const double p[3])
  * surface attaining it (lowest region index on ties, box = -1 last). */
 typedef struct { double dmin; double dstar; int istar; int region; double dbox; double dsoft; } or_eval;
 
-/* 1 if region r's program contains a smooth union (its boundary is then not
- * made of primitive boundaries). */
+/* Segment stepping bounds a region by rays to its primitives, widened by a
+ * margin of k/4 per smooth union (below).  A region with more smooth unions
+ * than this ("soft") keeps the isotropic bound |d| - delta/2: its margin
+ * would grow past what the ray bound gains. */
+#define OR_SEG_MAX_SMOOTH 8
+
 static int region_soft(const or_scene *S, int r)
 {
     const or_region *R = &S->regions[r];
+    int n = 0;
     for (int i = 0; i < R->count; ++i)
-        if (S->nodes[R->begin + i].op == 2) return 1;
-    return 0;
+        if (S->nodes[R->begin + i].op == 2) n += 1;
+    return n > OR_SEG_MAX_SMOOTH;
 }
 
 static or_eval scene_eval(const or_scene *S, const double p[3], or_totals *T)
 {
     or_eval E;
     E.dmin = INFINITY; E.dstar = 0.0; E.istar = -1; E.region = -1;
-    E.dsoft = INFINITY;      /* min |d| over regions with a smooth union */
+    E.dsoft = INFINITY;      /* min |d| over soft regions */
     for (int r = 0; r < S->nregions; ++r) {
         double d = region_sdf(S, r, p, T);
         if (d < 0.0) E.region = r;
@@ -645,19 +651,43 @@ static void launch(const or_source *src, double p[3], double u[3], double *tau, 
  * lengthens sphere-tracing steps with bounds taken along the ray, as the
  * remedy for the many small steps of packets travelling nearly parallel to
  * a surface).  Sphere tracing moves by d_min, a bound valid in every
- * direction.  Along the packet's own direction u a longer move is safe:
- *   - sphere, box: t = distance along the ray to the surface offset by
- *     delta/2 (grown when p is outside, shrunk when inside).  On [0, t) the
- *     primitive's |SDF| stays above delta/2, so its sign cannot change;
- *   - a region built by hard CSG (union = min, intersection = max,
- *     subtraction = max(a, -b)) changes sign only where one of its
- *     primitives does, so the minimum of t over its primitives bounds it;
- *   - regions with a smooth union, and capsules: the isotropic |d| - delta/2;
- *   - the bounding box: its exit distance, shrunk by delta/2.
- * The step is max(d_min - delta/2, minimum of the bounds): never shorter
- * than plain sphere tracing.  It ends delta/2 short of the first surface,
- * where the next evaluation finds d_min < delta and the interface routine
- * of Sec. 2.3 runs unchanged.
+ * direction.  Along the packet's own direction u a longer move is safe.
+ *
+ * Margin of a region: M = sum of k/4 over its smooth unions (0 for hard
+ * CSG).  A smooth union lies between min(a, b) - k/4 and min(a, b) (the
+ * blend term k h (1 - h) peaks at h = 1/2), and min, max and max(a, -b)
+ * move by at most the largest change of their operands, so the region's
+ * SDF F stays within M of its hard version H (every smooth union replaced
+ * by min).  H takes, at each point, the value or the negated value of one
+ * of its primitives; hence F = 0 only where some primitive has |d_i| <= M.
+ * A three-fold smooth union of one sphere reaches 0.39 k below min, so the
+ * sum over the folds, not a single k/4, is needed.  Soft regions (more than
+ * OR_SEG_MAX_SMOOTH smooth unions) take their isotropic |d| - delta/2.
+ *
+ * Primitive bound with margin e = M + delta/2 (M the largest margin of the
+ * regions that use the primitive): the distance along the ray until |d_i|
+ * can fall to e:
+ *   - sphere, box, capsule, capped cylinder: outside, the entry of the shape
+ *     grown by e (for boxes and cylinders the grown box, which holds the
+ *     rounded one); inside, the exit of the shape shrunk by e (exactly the
+ *     set d_i < -e of these convex shapes);
+ *   - torus from outside: the entry of the annular slab that holds the tube
+ *     grown by e, and at least d_i - e; from inside, d_i's own |d_i| - e;
+ *   - the same shapes placed by a frame without a domain operation, in the
+ *     frame's coordinates; domain operations: |d_i| - e.
+ * On [0, t) every primitive keeps |d_i| > e, so no region's sign changes and
+ * every region's |F| stays above delta/2.  The bounding box adds its exit
+ * distance, shrunk by delta/2.  The step is max(d_min - delta/2, minimum of
+ * the bounds): never shorter than plain sphere tracing.  It ends delta/2
+ * short of the first surface, where the next evaluation finds d_min < delta
+ * and the interface routine of Sec. 2.3 runs unchanged.
+ *
+ * The primitives of the regions that are not soft are visited once each,
+ * in the order of first use by those regions, after the bounding box and
+ * the soft regions' bound.  A primitive whose |d_i| - e is not
+ * below the bound so far cannot lower it (its ray bound is at least that,
+ * the SDF being 1-Lipschitz) and is passed over; one with |d_i| <= e ends
+ * the search with 0.
  * ---------------------------------------------------------------------- */
 static double segment_sphere(const double *q, double d, const double p[3], const double u[3], double dh)
 {
@@ -789,14 +819,63 @@ static double segment_capsule(const double *q, double d, const double p[3], cons
     return t > 0.0 ? t : 0.0;
 }
 
-/* A sphere, box or capsule placed by a frame without a domain operation:
- * the frame (rotation R, translation t, uniform scale s) maps the ray
- * p + t' u to the local ray q + (t' / s) w with q = R^T (p - t) / s and the
- * unit direction w = R^T u, and local distances are world distances over s.
- * So the world bound is s times the local bound with margin dh / s; only the
- * sign of d is used. */
+/* Capped cylinder along z (radius q[3], half height q[4]): convex, the
+ * slab |z - c_z| <= h cut by the infinite cylinder; grown by e from outside,
+ * shrunk by e from inside (the margin's sign follows d). */
+static double segment_cylinder(const double *q, double d, const double p[3], const double u[3], double e)
+{
+    double g = d > 0.0 ? e : -e;
+    double rr = q[3] + g, hh = q[4] + g;
+    double t0, t1;
+    ray_cylinder(p[0] - q[0], p[1] - q[1], p[2] - q[2] + hh, 0.0, 0.0, 2.0 * hh, 4.0 * hh * hh, rr, u, &t0, &t1);
+    if (d > 0.0) {
+        if (!(t0 <= t1) || t1 < 0.0) return INFINITY;
+        return t0 > 0.0 ? t0 : 0.0;
+    }
+    if (!(t0 <= t1)) return 0.0;
+    return t1 > 0.0 ? t1 : 0.0;
+}
+
+/* Torus about z (major radius q[3], tube q[4]) from outside: the tube grown
+ * by e lies in the annular slab R - r' <= rho <= R + r', |z - c_z| <= r'
+ * (r' = r + e); the ray's first point in that slab, and never less than
+ * d - e.  From inside the tube: |d| - e. */
+static double segment_torus(const double *q, double d, const double p[3], const double u[3], double e)
+{
+    if (d < 0.0) return -d - e;
+    double R = q[3], rt = q[4] + e;
+    double ox = p[0] - q[0], oy = p[1] - q[1], oz = p[2] - q[2] + rt;
+    double a0, a1;
+    ray_cylinder(ox, oy, oz, 0.0, 0.0, 2.0 * rt, 4.0 * rt * rt, R + rt, u, &a0, &a1);
+    double lo = fmax(a0, 0.0), hi = a1;
+    if (!(lo <= hi)) return INFINITY;
+    if (R - rt > 0.0) {                  /* the hole rho < R - r' is not in the slab */
+        double b0, b1;
+        ray_cylinder(ox, oy, oz, 0.0, 0.0, 2.0 * rt, 4.0 * rt * rt, R - rt, u, &b0, &b1);
+        if (b0 <= lo && lo < b1) lo = b1;
+        if (!(lo < hi)) return INFINITY;   /* left the slab inside the hole */
+    }
+    return fmax(lo, d - e);
+}
+
+/* The shape kinds with a ray bound, in the primitive's own coordinates. */
+static double segment_base(int kind, const double *q, double d, const double p[3], const double u[3], double e)
+{
+    if (kind == 0) return segment_sphere(q, d, p, u, e);
+    if (kind == 1) return segment_box(q, q + 3, d, p, u, e);
+    if (kind == 2) return segment_capsule(q, d, p, u, e);
+    if (kind == 3) return segment_torus(q, d, p, u, e);
+    return segment_cylinder(q, d, p, u, e);
+}
+
+/* A primitive placed by a frame without a domain operation: the frame
+ * (rotation R, translation t, uniform scale s) maps the ray p + t' u to the
+ * local ray q + (t' / s) w with q = R^T (p - t) / s and the unit direction
+ * w = R^T u, and local distances are world distances over s.  So the world
+ * bound is s times the local bound with margin e / s; only the sign of d and
+ * (for the torus) its value over s are used. */
 static double segment_xprim(const or_prim *pr, const or_xform *X, double d, const double p[3], const double u[3],
-                            double dh)
+                            double e)
 {
     double vx = p[0] - X->t[0], vy = p[1] - X->t[1], vz = p[2] - X->t[2];
     double q[3], w[3];
@@ -806,24 +885,57 @@ static double segment_xprim(const or_prim *pr, const or_xform *X, double d, cons
     w[0] = X->rot[0] * u[0] + X->rot[3] * u[1] + X->rot[6] * u[2];
     w[1] = X->rot[1] * u[0] + X->rot[4] * u[1] + X->rot[7] * u[2];
     w[2] = X->rot[2] * u[0] + X->rot[5] * u[1] + X->rot[8] * u[2];
-    double hl = dh / X->s, t;
-    if (pr->kind == 0) t = segment_sphere(pr->p, d, q, w, hl);
-    else if (pr->kind == 1) t = segment_box(pr->p, pr->p + 3, d, q, w, hl);
-    else t = segment_capsule(pr->p, d, q, w, hl);
-    return X->s * t;
+    return X->s * segment_base(pr->kind, pr->p, d / X->s, q, w, e / X->s);
 }
 
-static double segment_prim(const or_scene *S, const or_prim *pr, const double p[3], const double u[3],
-                           double dh)
+/* Bound of one primitive whose distance d satisfies |d| > e. */
+static double segment_prim(const or_scene *S, const or_prim *pr, double d, const double p[3], const double u[3],
+                           double e)
 {
-    double d = sdf_prim(S, pr, p);
-    if (!(fabs(d) > dh)) return 0.0;
-    if (pr->xform == 0 && pr->kind == 0) return segment_sphere(pr->p, d, p, u, dh);
-    if (pr->xform == 0 && pr->kind == 1) return segment_box(pr->p, pr->p + 3, d, p, u, dh);
-    if (pr->xform == 0 && pr->kind == 2) return segment_capsule(pr->p, d, p, u, dh);
-    if (pr->xform > 0 && pr->kind <= 2 && S->xforms[pr->xform - 1].op == 0)
-        return segment_xprim(pr, &S->xforms[pr->xform - 1], d, p, u, dh);
-    return fabs(d) - dh;                 /* other shapes, domain operations: isotropic bound */
+    if (pr->xform == 0) return segment_base(pr->kind, pr->p, d, p, u, e);
+    if (S->xforms[pr->xform - 1].op == 0) return segment_xprim(pr, &S->xforms[pr->xform - 1], d, p, u, e);
+    return fabs(d) - e;                  /* domain operations: isotropic bound */
+}
+
+/* Sum of k/4 over the smooth unions of region r (0: hard CSG). */
+static double region_margin(const or_scene *S, int r)
+{
+    const or_region *R = &S->regions[r];
+    double m = 0.0;
+    for (int i = 0; i < R->count; ++i)
+        if (S->nodes[R->begin + i].op == 2) m = m + 0.25 * S->nodes[R->begin + i].k;
+    return m;
+}
+
+/* 1 if node i of region r is the first use of its primitive by a region
+ * that is not soft (regions in order, nodes in program order). */
+static int first_use(const or_scene *S, int r, int i)
+{
+    int prim = S->nodes[S->regions[r].begin + i].prim;
+    for (int r2 = 0; r2 <= r; ++r2) {
+        if (region_soft(S, r2)) continue;
+        const or_region *R = &S->regions[r2];
+        int end = r2 == r ? i : R->count;
+        for (int j = 0; j < end; ++j)
+            if (S->nodes[R->begin + j].op == 0 && S->nodes[R->begin + j].prim == prim) return 0;
+    }
+    return 1;
+}
+
+/* Largest margin of the regions, not soft, that use primitive prim. */
+static double prim_margin(const or_scene *S, int prim)
+{
+    double m = 0.0;
+    for (int r = 0; r < S->nregions; ++r) {
+        if (region_soft(S, r)) continue;
+        const or_region *R = &S->regions[r];
+        for (int j = 0; j < R->count; ++j)
+            if (S->nodes[R->begin + j].op == 0 && S->nodes[R->begin + j].prim == prim) {
+                m = fmax(m, region_margin(S, r));
+                break;
+            }
+    }
+    return m;
 }
 
 /* Largest safe move from p along u (scene evaluated at p in E). */
@@ -831,22 +943,27 @@ static double segment_bound(const or_scene *S, const or_eval *E, const double p[
                             or_totals *T)
 {
     double dh = 0.5 * S->delta;
-    double t = E->dsoft - dh;
+    double c[3], h[3];
+    bbox_center_half(S, c, h);
+    double t = fmin(segment_box(c, h, E->dbox, p, u, dh), E->dsoft - dh);
     if (T) T->seg_calls += 1;
     for (int r = 0; r < S->nregions; ++r) {
         if (region_soft(S, r)) continue;
         const or_region *R = &S->regions[r];
         for (int i = 0; i < R->count; ++i) {
             const or_node *nd = &S->nodes[R->begin + i];
-            if (nd->op == 0) {
-                t = fmin(t, segment_prim(S, &S->prims[nd->prim], p, u, dh));
-                if (T) T->seg_kind[S->prims[nd->prim].kind] += 1;
-            }
+            if (nd->op != 0 || !first_use(S, r, i)) continue;
+            const or_prim *pr = &S->prims[nd->prim];
+            double e = prim_margin(S, nd->prim) + dh;
+            double d = sdf_prim(S, pr, p);
+            if (T) T->seg_dist[pr->kind] += 1;
+            if (!(fabs(d) > e)) return 0.0;
+            if (fabs(d) - e >= t) continue;
+            t = fmin(t, segment_prim(S, pr, d, p, u, e));
+            if (T) T->seg_kind[pr->kind] += 1;
         }
     }
-    double c[3], h[3];
-    bbox_center_half(S, c, h);
-    return fmin(t, segment_box(c, h, E->dbox, p, u, dh));
+    return t;
 }
 
 #define OR_W_ROULETTE 1e-4

@@ -67,8 +67,20 @@ MUTANTS = [
     ("segment_cylinder_cross_axis", "double vx = u[0] - k * bax, vy = u[1] - k * bay, vz = u[2] - k * baz;",
      "double vx = u[0], vy = u[1], vz = u[2];"),
     ("segment_capsule_exit", "if (t0[k] <= t1[k]) t = fmax(t, t1[k]);", "if (t0[k] <= t1[k]) t = fmax(t, t0[k]);"),
-    ("segment_xprim_margin", "double hl = dh / X->s, t;", "double hl = dh, t;"),
-    ("segment_xprim_scale", "    return X->s * t;\n", "    return t;\n"),
+    ("segment_xprim_margin", "segment_base(pr->kind, pr->p, d / X->s, q, w, e / X->s);",
+     "segment_base(pr->kind, pr->p, d / X->s, q, w, e);"),
+    ("segment_xprim_scale", "return X->s * segment_base(", "return segment_base("),
+    # smooth-union margin: one fold's k/4 instead of the sum over the folds
+    ("segment_fold_margin", "m = m + 0.25 * S->nodes[R->begin + i].k;", "m = 0.25 * S->nodes[R->begin + i].k;"),
+    ("segment_margin_unused", "double e = prim_margin(S, nd->prim) + dh;", "double e = dh;"),
+    # passing over a primitive whose own distance (not less the margin)
+    # reaches the bound so far
+    ("segment_prune_margin", "if (fabs(d) - e >= t) continue;", "if (fabs(d) >= t) continue;"),
+    ("segment_cylinder_cap", "double rr = q[3] + g, hh = q[4] + g;", "double rr = q[3] + g, hh = q[4];"),
+    ("segment_cylinder_exit", "    return t1 > 0.0 ? t1 : 0.0;\n}\n\n/* Torus", "    return t0 > 0.0 ? t0 : 0.0;\n}\n\n/* Torus"),
+    ("segment_torus_growth", "double R = q[3], rt = q[4] + e;", "double R = q[3], rt = q[4];"),
+    ("segment_torus_hole", "if (b0 <= lo && lo < b1) lo = b1;", "if (0) lo = b1;"),
+    ("segment_torus_inside", "if (d < 0.0) return -d - e;", "if (d < 0.0) return -d;"),
     ("segment_xprim_direction", "w[0] = X->rot[0] * u[0] + X->rot[3] * u[1] + X->rot[6] * u[2];",
      "w[0] = X->rot[0] * u[0] + X->rot[1] * u[1] + X->rot[2] * u[2];"),
 ]

@@ -1060,6 +1060,144 @@ def test_segment_step_exact_for_placed_primitives():
     assert math.isclose(O.segment_step(el, p, down), e["dmin"] - d / 2, rel_tol=1e-12)
 
 
+def _brute_force_move(sc, p, u, t, n=400):
+    """Every region keeps its sign along the move and the scene distance
+    stays >= delta/2 (sampled densely)."""
+    p = np.asarray(p, dtype=float)
+    signs = [np.sign(O.region_sdf(sc, r, p)) for r in range(len(sc.regions))]
+    for s in np.linspace(0.0, t, n):
+        q = p + s * u
+        e = O.scene_eval(sc, q)
+        assert e["dmin"] >= 0.5 * sc.delta - 1e-12, (p, u, t, s, e)
+        assert [np.sign(O.region_sdf(sc, r, q)) for r in range(len(sc.regions))] == signs, (p, u, t, s)
+
+
+def _one_region(prims, program, lo=(-5, -5, -5), hi=(5, 5, 5), d=1e-3):
+    return W.Scene(tuple(prims), (W.Region(program, 0.0, 1.0, 0.0, 1.5),), 1.0, lo, hi, delta=d,
+                   stepping=W.SEGMENT)
+
+
+def test_segment_step_smooth_fold_margin():
+    # three smooth unions of one sphere with itself: the blend adds up to
+    # k/4 + k h (1 - h) + ... below min; for equal operands the fold gives
+    # a - k/4, then a - k (5/32 + 15/64) = a - 0.390625 k, so the surface is
+    # at radius r + 0.390625 k, beyond the r + k/4 a single margin would take
+    r, k, d = 0.3, 0.2, 1e-3
+    sph = W.Prim(W.SPHERE, (0.0, 0.0, 0.0, r))
+    prog = (W.Node(W.PRIM, 0), W.Node(W.PRIM, 1), W.Node(W.SMOOTH_UNION, -1, k),
+            W.Node(W.PRIM, 2), W.Node(W.SMOOTH_UNION, -1, k))
+    sc = _one_region([sph, sph, sph], prog, d=d)
+    rs = r + 0.390625 * k
+    assert abs(O.region_sdf(sc, 0, (0.0, 0.0, rs))) < 1e-12
+    down = np.array([0.0, 0.0, -1.0])
+    # the margin is the sum over both folds, k/2: a ray passing the centre
+    # at a distance below r + k/2 + delta/2 stops on that grown sphere
+    # (longer than the isotropic step), also where it would miss the
+    # surface itself, and where a k/4 margin would let it cross the surface
+    for x0 in (0.36, 0.39):
+        t = O.segment_step(sc, (x0, 0.0, 2.0), down)
+        rg = r + 0.5 * k + d / 2
+        assert math.isclose(t, 2.0 - math.sqrt(rg * rg - x0 * x0), rel_tol=1e-12)
+        _brute_force_move(sc, (x0, 0.0, 2.0), down, t)
+    # past the grown sphere: only the bounding box bounds the move
+    assert math.isclose(O.segment_step(sc, (0.45, 0.0, 2.0), down), 7.0 - d / 2, rel_tol=1e-12)
+    # oblique rays that graze the blended surface
+    rng = np.random.default_rng(11)
+    for _ in range(40):
+        p = rng.normal(size=3)
+        p *= 1.5 / np.linalg.norm(p)
+        aim = rng.normal(0.0, 0.3, 3)
+        u = (aim - p) / np.linalg.norm(aim - p)
+        t = O.segment_step(sc, p, u)
+        _brute_force_move(sc, p, u, t, n=200)
+    # two spheres side by side, a ray down their bisecting plane: the blend
+    # reaches k/4 below both (equal operands) and the surface lies on the
+    # spheres grown by k/4
+    a, b = W.Prim(W.SPHERE, (-0.05, 0.0, 0.0, 0.2)), W.Prim(W.SPHERE, (0.05, 0.0, 0.0, 0.2))
+    two = _one_region([a, b], (W.Node(W.PRIM, 0), W.Node(W.PRIM, 1), W.Node(W.SMOOTH_UNION, -1, k)), d=d)
+    zs = math.sqrt(0.25 ** 2 - 0.05 ** 2)
+    assert abs(O.region_sdf(two, 0, (0.0, 0.0, zs))) < 1e-12
+    t = O.segment_step(two, (0.0, 0.0, 1.0), down)
+    ze = math.sqrt((0.25 + d / 2) ** 2 - 0.05 ** 2)
+    assert math.isclose(t, 1.0 - ze, rel_tol=1e-12)
+    # a bounding box whose exit lies past the blended surface but short of the
+    # spheres' own distance: the spheres are not passed over as unable to bind
+    cut = W.Scene((a, b), (W.Region(two.regions[0].program, 0.0, 1.0, 0.0, 1.5),), 1.0, (-2, -2, 0.22),
+                  (2, 2, 2), delta=d, stepping=W.SEGMENT)
+    t = O.segment_step(cut, (0.0, 0.0, 1.0), down)
+    assert math.isclose(t, 1.0 - ze, rel_tol=1e-12)
+    _brute_force_move(cut, (0.0, 0.0, 1.0), down, t)
+    # more than eight smooth unions: the region keeps its isotropic bound
+    many = [W.Prim(W.SPHERE, (0.1 * i, 0.0, 0.0, 0.2)) for i in range(10)]
+    prog = [W.Node(W.PRIM, 0)]
+    for i in range(1, 10):
+        prog += [W.Node(W.PRIM, i), W.Node(W.SMOOTH_UNION, -1, 0.05)]
+    soft = _one_region(many, tuple(prog), d=d)
+    p = (0.45, 0.0, 2.0)
+    e = O.scene_eval(soft, p)
+    assert math.isclose(O.segment_step(soft, p, down), e["dmin"] - d / 2, rel_tol=1e-12)
+
+
+def test_segment_step_exact_for_cylinders_and_tori():
+    d = 1e-3
+    down = np.array([0.0, 0.0, -1.0])
+    cyl = _one_region([W.Prim(W.CYLINDER, (0.0, 0.0, 0.0, 0.3, 0.5))], W.prim_program([0]), d=d)
+    # outside: the cylinder grown by delta/2 in radius and half height
+    assert math.isclose(O.segment_step(cyl, (0.1, 0.0, 2.0), down), 2.0 - (0.5 + d / 2), rel_tol=1e-12)
+    assert math.isclose(O.segment_step(cyl, (2.0, 0.0, 0.2), np.array([-1.0, 0.0, 0.0])), 2.0 - (0.3 + d / 2),
+                        rel_tol=1e-12)
+    # a ray past the rim (cap plane reached outside the grown radius) goes on
+    # to the side wall
+    u = np.array([-1.0, 0.0, -1.0]) / math.sqrt(2.0)
+    t = O.segment_step(cyl, (1.5, 0.0, 1.0), u)
+    assert math.isclose(t, (1.5 - (0.3 + d / 2)) * math.sqrt(2.0), rel_tol=1e-12)
+    # inside: the exit of the cylinder shrunk by delta/2
+    assert math.isclose(O.segment_step(cyl, (0.0, 0.0, 0.0), np.array([0.0, 0.0, 1.0])), 0.5 - d / 2,
+                        rel_tol=1e-12)
+    assert math.isclose(O.segment_step(cyl, (0.0, 0.0, 0.0), np.array([1.0, 0.0, 0.0])), 0.3 - d / 2,
+                        rel_tol=1e-12)
+    tor = _one_region([W.Prim(W.TORUS, (0.0, 0.0, 0.0, 0.5, 0.15))], W.prim_program([0]), d=d)
+    # outside, in the ring's plane and from above the core circle: d - delta/2
+    assert math.isclose(O.segment_step(tor, (2.0, 0.0, 0.0), np.array([-1.0, 0.0, 0.0])), 2.0 - 0.65 - d / 2,
+                        rel_tol=1e-12)
+    assert math.isclose(O.segment_step(tor, (0.5, 0.0, 1.0), down), 1.0 - 0.15 - d / 2, rel_tol=1e-12)
+    # down the axis through the hole: only the bounding box bounds the move
+    assert math.isclose(O.segment_step(tor, (0.0, 0.0, 1.0), down), 6.0 - d / 2, rel_tol=1e-12)
+    # inside the tube: the isotropic bound
+    assert math.isclose(O.segment_step(tor, (0.5, 0.0, 0.05), np.array([1.0, 0.0, 0.0])), 0.1 - d / 2,
+                        rel_tol=1e-12)
+    # placed by a frame (quarter turn about x, scale 2): the ring's axis is
+    # world y, so a ray down world y through the hole meets nothing
+    rx = W.rotation((1, 0, 0), 90.0)
+    ptor = _one_region([W.Prim(W.TORUS, (0.0, 0.0, 0.0, 0.5, 0.15), W.Xform(rot=rx, t=(0.0, 0.0, -1.0), s=2.0))],
+                       W.prim_program([0]), d=d)
+    assert math.isclose(O.segment_step(ptor, (0.0, 3.0, -1.0), np.array([0.0, -1.0, 0.0])), 8.0 - d / 2,
+                        rel_tol=1e-12)
+    assert math.isclose(O.segment_step(ptor, (0.0, 0.0, 2.0), down), 3.0 - 2.0 * 0.65 - d / 2, rel_tol=1e-12)
+    pcyl = _one_region([W.Prim(W.CYLINDER, (0.0, 0.0, 0.0, 0.3, 0.5), W.Xform(rot=rx, t=(0.0, 0.0, -1.0), s=1.5))],
+                       W.prim_program([0]), d=d)
+    # the cylinder's axis is world y: from above, its side at 1.5 * 0.3
+    assert math.isclose(O.segment_step(pcyl, (0.0, 0.2, 2.0), down), 3.0 - (1.5 * 0.3 + d / 2), rel_tol=1e-12)
+    # brute force from random points and directions, hard CSG of both
+    both = W.Scene((W.Prim(W.TORUS, (0.0, 0.0, 0.0, 0.5, 0.15)), W.Prim(W.CYLINDER, (0.4, 0.0, 0.1, 0.2, 0.3)),
+                    W.Prim(W.TORUS, (0.0, 0.0, 0.0, 0.4, 0.1), W.Xform(rot=W.rotation((1, 1, 0), 60.0),
+                                                                      t=(-0.3, 0.2, 0.0)))),
+                   (W.Region((W.Node(W.PRIM, 0), W.Node(W.PRIM, 1), W.Node(W.SUBTRACT)), 0.0, 1.0, 0.0, 1.5),
+                    W.Region(W.prim_program([2]), 0.0, 1.0, 0.0, 1.3)),
+                   1.0, (-1.2, -1.2, -1.2), (1.2, 1.2, 1.2), delta=d, stepping=W.SEGMENT)
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(150):
+        p = rng.uniform(-1.1, 1.1, 3)
+        if O.scene_eval(both, p)["dmin"] < d:
+            continue
+        aim = rng.normal(0.0, 0.4, 3)
+        u = (aim - p) / np.linalg.norm(aim - p)
+        _brute_force_move(both, p, u, O.segment_step(both, p, u), n=200)
+        checked += 1
+    assert checked > 100
+
+
 def _seg(sc):
     from dataclasses import replace
     return replace(sc, stepping=W.SEGMENT)
