@@ -4,8 +4,10 @@ Translation units and their floating-point flags:
   smcrt_k64.cu   FP64 packet kernel, -fmad=false (no FMA contraction, so the
                  kernel's arithmetic is the reference's IEEE sequence);
   smcrt_k32.cu   mixed kernel, approximate FP32 division/sqrt, FTZ; the
-                 multiply-adds are fused where the front end writes them
-                 (explicit FMAs in the PTX) and nowhere else: the assembler
+                 multiply-adds are fused where the source writes them
+                 (__fmaf_rn in the distances, moves, tally set-up and
+                 scattering: 3 % on the layered slab) or the front end
+                 contracts them, and nowhere else: the assembler
                  may not fuse plain multiply / add pairs (--fmad=false),
                  because it fused them differently under different register
                  budgets, and every instantiation must give the same bits;

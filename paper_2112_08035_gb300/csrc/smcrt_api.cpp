@@ -471,10 +471,15 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     const size_t o_coff = take(sizeof(int32_t) * cg.off.size());
     const size_t o_clist = take(sizeof(int32_t) * cg.list.size());
     std::vector<int32_t> segp(sc->stepping == SMCRT_STEP_SEGMENT ? kMaxPrims : 0);
-    // a culled region bounds segment moves by its (culled) distance, like a
+    std::vector<double> segm(segp.size());
+    // the culled region bounds segment moves by its (culled) distance, like a
     // soft region: ray bounds over all its primitives would undo the culling
-    const int nseg = segp.empty() ? 0 : hard_region_prims(sc, segp.data(), cg.region);
+    const int nseg = segp.empty() ? 0 : seg_entries(sc, segp.data(), segm.data(), cg.region);
+    std::vector<float> segm32(nseg);
+    for (int j = 0; j < nseg; ++j) segm32[j] = (float)segm[j];
     const size_t o_seg = take(sizeof(int32_t) * nseg);
+    const size_t o_segm64 = take(sizeof(double) * nseg);
+    const size_t o_segm32 = take(sizeof(float) * nseg);
     const size_t o_xf64 = take(sizeof(double) * xf64.size());
     const size_t o_xf32 = take(sizeof(float4) * xf32.size());
     const size_t total = off;
@@ -531,6 +536,8 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     H.stepping = sc->stepping;
     H.nseg = nseg;
     H.seg_prims = nseg > 0 ? (const int32_t *)(base + o_seg) : nullptr;
+    H.seg_m64 = nseg > 0 ? (const double *)(base + o_segm64) : nullptr;
+    H.seg_m32 = nseg > 0 ? (const float *)(base + o_segm32) : nullptr;
     H.xf64 = has_xf ? (const double *)(base + o_xf64) : nullptr;
     H.xf32 = has_xf ? (const float4 *)(base + o_xf32) : nullptr;
     for (int i = 0; i < np; ++i) H.general = H.general || !plain_prim(sc->prims[i]);
@@ -581,7 +588,11 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
     std::memcpy(hb.data() + o_r32, reg32.data(), sizeof(float4) * 2 * nr);
     if (!cg.off.empty()) std::memcpy(hb.data() + o_coff, cg.off.data(), sizeof(int32_t) * cg.off.size());
     if (!cg.list.empty()) std::memcpy(hb.data() + o_clist, cg.list.data(), sizeof(int32_t) * cg.list.size());
-    if (nseg > 0) std::memcpy(hb.data() + o_seg, segp.data(), sizeof(int32_t) * nseg);
+    if (nseg > 0) {
+        std::memcpy(hb.data() + o_seg, segp.data(), sizeof(int32_t) * nseg);
+        std::memcpy(hb.data() + o_segm64, segm.data(), sizeof(double) * nseg);
+        std::memcpy(hb.data() + o_segm32, segm32.data(), sizeof(float) * nseg);
+    }
     if (has_xf) {
         std::memcpy(hb.data() + o_xf64, xf64.data(), sizeof(double) * xf64.size());
         std::memcpy(hb.data() + o_xf32, xf32.data(), sizeof(float4) * xf32.size());

@@ -3,6 +3,7 @@
 // Not part of the public C-ABI.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -86,25 +87,42 @@ inline void fill_prim(const smcrt_scene *sc, int i, double *d, float4 *f, double
 // sphere, box, capsule in scene coordinates.
 inline bool plain_prim(const smcrt_prim &P) { return P.kind <= SMCRT_CAPSULE && P.xform <= 0; }
 
-// Segment stepping: the last instruction of a region whose program contains
-// a smooth union ("soft" region: its boundary is not made of primitive
-// boundaries, so only |d| bounds it) carries this bit in Instr.op.
+// Segment stepping bounds a region by rays to its primitives, widened by a
+// margin of k/4 per smooth union (a smooth union lies at most k/4 below
+// min, and min, max and subtraction move by at most their operands'
+// change, so the region's surface lies where some primitive has |d| <= the
+// sum).  A region with more smooth unions than kSegMaxSmooth ("soft") keeps
+// the isotropic bound |d| - delta/2; the last instruction of its program
+// carries kSoftRegionEnd in Instr.op.
+constexpr int kSegMaxSmooth = 8;
 constexpr int32_t kSoftRegionEnd = 0x10000;
 
 inline bool region_is_soft(const smcrt_scene *sc, int r)
 {
     const smcrt_region &R = sc->regions[r];
+    int n = 0;
     for (int i = 0; i < R.node_count; ++i)
-        if (sc->nodes[R.node_begin + i].op == SMCRT_OP_SMOOTH_UNION) return true;
-    return false;
+        if (sc->nodes[R.node_begin + i].op == SMCRT_OP_SMOOTH_UNION) ++n;
+    return n > kSegMaxSmooth;
 }
 
-// Distinct primitives of the hard (not soft) regions, in first-use order:
-// the primitives whose offset surfaces bound a segment-stepping move.
-// skip_region (the mixed kernel's culled region) is left out: its culled
-// distance bounds moves isotropically instead.
-// Writes at most kMaxPrims indices; no allocation.
-inline int hard_region_prims(const smcrt_scene *sc, int32_t *out, int skip_region = -1)
+// Sum of k/4 over region r's smooth unions, in program order (0: hard CSG).
+inline double region_margin(const smcrt_scene *sc, int r)
+{
+    const smcrt_region &R = sc->regions[r];
+    double m = 0.0;
+    for (int i = 0; i < R.node_count; ++i)
+        if (sc->nodes[R.node_begin + i].op == SMCRT_OP_SMOOTH_UNION) m = m + 0.25 * sc->nodes[R.node_begin + i].k;
+    return m;
+}
+
+// The primitives whose offset surfaces bound a segment-stepping move: the
+// distinct primitives of the regions that are not soft, in first-use order,
+// each with the largest margin of those regions that use it.  skip_region
+// (the mixed kernel's culled region) is left out: its culled distance
+// bounds moves isotropically (ray bounds over all its primitives would undo
+// the culling).  Writes at most kMaxPrims entries; no allocation.
+inline int seg_entries(const smcrt_scene *sc, int32_t *out, double *margin, int skip_region = -1)
 {
     uint64_t seen[kMaxPrims / 64] = {};
     int n = 0;
@@ -117,6 +135,17 @@ inline int hard_region_prims(const smcrt_scene *sc, int32_t *out, int skip_regio
             const uint64_t bit = 1ull << (nd.prim & 63);
             if (seen[nd.prim >> 6] & bit) continue;
             seen[nd.prim >> 6] |= bit;
+            double m = 0.0;
+            for (int r2 = 0; r2 < sc->nregions; ++r2) {
+                if (r2 == skip_region || region_is_soft(sc, r2)) continue;
+                const smcrt_region &Q = sc->regions[r2];
+                for (int j = 0; j < Q.node_count; ++j)
+                    if (sc->nodes[Q.node_begin + j].op == SMCRT_OP_PRIM && sc->nodes[Q.node_begin + j].prim == nd.prim) {
+                        m = std::fmax(m, region_margin(sc, r2));
+                        break;
+                    }
+            }
+            margin[n] = m;
             out[n++] = nd.prim;
         }
     }
@@ -170,8 +199,11 @@ struct DevScene {
     float cull_kinv;
     const int32_t *cull_off;  // G^3 + 1 prefix offsets into cull_list
     const int32_t *cull_list; // primitive indices, in the region's fold order
-    // Segment stepping (enum smcrt_stepping): the primitives of hard regions
+    // Segment stepping (enum smcrt_stepping): the bounding primitives and
+    // their margins (sum of k/4 over the smooth unions of their regions)
     const int32_t *seg_prims;
+    const double *seg_m64;
+    const float *seg_m32;
     int32_t stepping, nseg;
     // Primitive frames (kXf64 doubles / kXf32 float4 per primitive), null
     // when no primitive has one

@@ -77,15 +77,15 @@ __device__ __forceinline__ float hg_cos32(float g, float xi)
     if (fabsf(g) < 1e-6f) {
         c = 2.f * xi - 1.f;
     } else {
-        const float t = __fdividef(1.f - g * g, 1.f - g + 2.f * g * xi);
-        c = __fdividef(1.f + g * g - t * t, 2.f * g);
+        const float t = __fdividef(__fmaf_rn(-g, g, 1.f), __fmaf_rn(2.f * g, xi, 1.f - g));
+        c = __fdividef(__fmaf_rn(-t, t, __fmaf_rn(g, g, 1.f)), 2.f * g);
     }
     return fminf(fmaxf(c, -1.f), 1.f);
 }
 
 __device__ __forceinline__ void normalise32(float &x, float &y, float &z)
 {
-    const float il = rsqrtf(x * x + y * y + z * z);
+    const float il = rsqrtf(__fmaf_rn(x, x, __fmaf_rn(y, y, z * z)));
     x *= il; y *= il; z *= il;
 }
 
@@ -97,9 +97,9 @@ __device__ __forceinline__ void scatter32(float &ux, float &uy, float &uz, float
     float b1[3], b2[3];
     onb32(ux, uy, uz, b1, b2);
     const float a1 = st * cp, a2 = st * sp;
-    float vx = a1 * b1[0] + a2 * b2[0] + ct * ux;
-    float vy = a1 * b1[1] + a2 * b2[1] + ct * uy;
-    float vz = a1 * b1[2] + a2 * b2[2] + ct * uz;
+    float vx = __fmaf_rn(a1, b1[0], __fmaf_rn(a2, b2[0], ct * ux));
+    float vy = __fmaf_rn(a1, b1[1], __fmaf_rn(a2, b2[1], ct * uy));
+    float vz = __fmaf_rn(a1, b1[2], __fmaf_rn(a2, b2[2], ct * uz));
     normalise32(vx, vy, vz);
     ux = vx; uy = vy; uz = vz;
 }
@@ -781,18 +781,18 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
             const float seg = interact ? tau * imu_t : L;
             long long *const flu = (long long *)jc->flu;
             // the segment starts back at the surface after a crossing (pend)
-            if (flu) tally32(S, flu, px - pend * ux, py - pend * uy, pz - pend * uz, ux, uy, uz, seg + pend, w,
-                             &npieces);
+            if (flu) tally32(S, flu, __fmaf_rn(-pend, ux, px), __fmaf_rn(-pend, uy, py), __fmaf_rn(-pend, uz, pz), ux,
+                             uy, uz, seg + pend, w, &npieces);
             pend = 0.f;
             if (SMCRT_RARE(crawl)) {
                 if (cs < 0.f) { qx = px; qy = py; qz = pz; cs = 0.f; }
                 cs += seg;
                 px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
             } else {
-                px += seg * ux; py += seg * uy; pz += seg * uz;
+                px = __fmaf_rn(seg, ux, px); py = __fmaf_rn(seg, uy, py); pz = __fmaf_rn(seg, uz, pz);
                 cs = -1.f;
             }
-            tau -= mu_t * seg;
+            tau = __fmaf_rn(-mu_t, seg, tau);
             phase = kTrace;
             iter_done = true;
         }

@@ -178,7 +178,7 @@ __device__ __forceinline__ float box32(float x, float y, float z, float cx, floa
 {
     const float qx = fabsf(x - cx) - hx, qy = fabsf(y - cy) - hy, qz = fabsf(z - cz) - hz;
     const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
-    const float outside = sqrtf(mx * mx + my * my + mz * mz);
+    const float outside = sqrtf(__fmaf_rn(mx, mx, __fmaf_rn(my, my, mz * mz)));
     const float inside = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
     return outside + inside;
 }
@@ -285,16 +285,16 @@ __device__ __forceinline__ float base32(int kind, const float4 *P, float x, floa
     const float4 A = (*(P));
     if (kind == 0) {
         const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
-        return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
+        return sqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz))) - A.w;
     }
     const float4 B = (*(P + 1));
     if (kind == 1) return box32(x, y, z, A.x, A.y, A.z, B.x, B.y, B.z);
     if (!G || kind == 2) {
         const float pax = x - A.x, pay = y - A.y, paz = z - A.z;
-        float t = (pax * B.x + pay * B.y + paz * B.z) * B.w;
+        float t = __fmaf_rn(pax, B.x, __fmaf_rn(pay, B.y, paz * B.z)) * B.w;
         t = fminf(fmaxf(t, 0.f), 1.f);
-        const float dx = pax - B.x * t, dy = pay - B.y * t, dz = paz - B.z * t;
-        return sqrtf(dx * dx + dy * dy + dz * dz) - A.w;
+        const float dx = __fmaf_rn(-B.x, t, pax), dy = __fmaf_rn(-B.y, t, pay), dz = __fmaf_rn(-B.z, t, paz);
+        return sqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz))) - A.w;
     }
     return round32(kind, P, x, y, z);
 }
@@ -500,7 +500,7 @@ __device__ __forceinline__ Eval32 scene_eval32(const DevScene &S, float x, float
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     for (int i = 0; i < S.ninstr; ++i) {
         if (i == cb) {
-            // the culled region's distance always bounds segment moves
+            // the culled region's distance bounds segment moves
             // isotropically (its primitives are not in seg_prims)
             region_end32(&E, S.cull_region, culled_region32(S, x, y, z), sel, true);
             i = ce - 1;
@@ -672,14 +672,16 @@ __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, 
 // ---------------------------------------------------------------------------
 // Segment stepping (scene option; Sec. 5 names segment tracing for packets
 // moving nearly parallel to a surface).  Bound on the move along u: for each
-// sphere and box of a hard-CSG region, the distance along the ray to its
-// surface offset by delta/2 (grown when p is outside, shrunk when inside),
-// over which the primitive's |SDF| stays above delta/2 and its sign cannot
-// change; the same for capsules (cylinder and end balls) and for those three
-// shapes placed by a frame without a domain operation; |d| - delta/2 for
-// soft regions (dsoft) and other shapes; the exit of the bounding box shrunk
-// by delta/2.  The caller moves max(d_min - delta/2,
-// bound).  FP64: the reference's operations in its order.
+// primitive of a region that is not soft, the distance along the ray until
+// its |SDF| can fall to e = m + delta/2, m the sum of k/4 over its regions'
+// smooth unions (a region's surface lies where some primitive has |d| <= m):
+// spheres, boxes, capsules and capped cylinders grown by e from outside and
+// shrunk by e from inside, tori from outside through the annular slab that
+// holds the grown tube, the same shapes placed by a frame without a domain
+// operation, |d| - e otherwise; |d| - delta/2 for soft regions (dsoft); the
+// exit of the bounding box shrunk by delta/2.  The caller moves
+// max(d_min - delta/2, bound).  FP64: the reference's operations in its
+// order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double seg_sphere64(const double *P, double d, double px, double py, double pz,
                                                double ux, double uy, double uz, double dh)
@@ -824,15 +826,57 @@ static __device__ __noinline__ double seg_capsule64(const double *P, double d, d
     return t > 0.0 ? t : 0.0;
 }
 
-// A sphere, box or capsule placed by a frame without a domain operation:
-// the local ray q + (t / s) w (q = R^T (p - t) / s, w = R^T u) and the local
-// bound with margin dh / s, times s; other frames keep the isotropic bound.
+// Capped cylinder along z (radius P[3], half height P[4]): the slab cut by
+// the cylinder, grown by e from outside, shrunk by e from inside.
+static __device__ __noinline__ double seg_cylinder64(const double *P, double d, double px, double py, double pz,
+                                                     double ux, double uy, double uz, double e)
+{
+    const double g = d > 0.0 ? e : -e;
+    const double rr = __ldg(P + 3) + g, hh = __ldg(P + 4) + g;
+    double t0, t1;
+    ray_cylinder64(px - __ldg(P), py - __ldg(P + 1), pz - __ldg(P + 2) + hh, 0.0, 0.0, 2.0 * hh, 4.0 * hh * hh, rr,
+                   ux, uy, uz, t0, t1);
+    if (d > 0.0) {
+        if (!(t0 <= t1) || t1 < 0.0) return __longlong_as_double(0x7ff0000000000000LL);
+        return t0 > 0.0 ? t0 : 0.0;
+    }
+    if (!(t0 <= t1)) return 0.0;
+    return t1 > 0.0 ? t1 : 0.0;
+}
+
+// Torus about z (major radius P[3], tube P[4]) from outside: the first point
+// of the ray in the annular slab that holds the tube grown by e, and never
+// less than d - e; from inside the tube, |d| - e.
+static __device__ __noinline__ double seg_torus64(const double *P, double d, double px, double py, double pz,
+                                                  double ux, double uy, double uz, double e)
+{
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    if (d < 0.0) return -d - e;
+    const double R = __ldg(P + 3), rt = __ldg(P + 4) + e;
+    const double ox = px - __ldg(P), oy = py - __ldg(P + 1), oz = pz - __ldg(P + 2) + rt;
+    double a0, a1;
+    ray_cylinder64(ox, oy, oz, 0.0, 0.0, 2.0 * rt, 4.0 * rt * rt, R + rt, ux, uy, uz, a0, a1);
+    double lo = fmax(a0, 0.0);
+    const double hi = a1;
+    if (!(lo <= hi)) return inf;
+    if (R - rt > 0.0) {                  // the hole is not in the slab
+        double b0, b1;
+        ray_cylinder64(ox, oy, oz, 0.0, 0.0, 2.0 * rt, 4.0 * rt * rt, R - rt, ux, uy, uz, b0, b1);
+        if (b0 <= lo && lo < b1) lo = b1;
+        if (!(lo < hi)) return inf;
+    }
+    return fmax(lo, d - e);
+}
+
+// A primitive placed by a frame without a domain operation: the local ray
+// q + (t / s) w (q = R^T (p - t) / s, w = R^T u) and the local bound of d / s
+// with margin e / s, times s; other frames keep the isotropic bound.
 static __device__ __noinline__ double seg_xprim64(const DevScene &S, int kind, int i, double d, double px,
                                                   double py, double pz, double ux, double uy, double uz,
-                                                  double dh)
+                                                  double e)
 {
     const double *X = S.xf64 + kXf64 * i;
-    if ((int)__ldg(X + 13) != 0 || kind > 2) return fabs(d) - dh;
+    if ((int)__ldg(X + 13) != 0) return fabs(d) - e;
     const double vx = px - __ldg(X + 9), vy = py - __ldg(X + 10), vz = pz - __ldg(X + 11);
     const double s = __ldg(X + 12);
     const double q0 = (__ldg(X) * vx + __ldg(X + 3) * vy + __ldg(X + 6) * vz) / s;
@@ -841,47 +885,57 @@ static __device__ __noinline__ double seg_xprim64(const DevScene &S, int kind, i
     const double w0 = __ldg(X) * ux + __ldg(X + 3) * uy + __ldg(X + 6) * uz;
     const double w1 = __ldg(X + 1) * ux + __ldg(X + 4) * uy + __ldg(X + 7) * uz;
     const double w2 = __ldg(X + 2) * ux + __ldg(X + 5) * uy + __ldg(X + 8) * uz;
-    const double hl = dh / s;
+    const double dl = d / s, el = e / s;
     const double *P = S.p64 + 8 * i;
     double t;
-    if (kind == 0) t = seg_sphere64(P, d, q0, q1, q2, w0, w1, w2, hl);
+    if (kind == 0) t = seg_sphere64(P, dl, q0, q1, q2, w0, w1, w2, el);
     else if (kind == 1)
-        t = seg_box64(__ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5), d, q0, q1, q2,
-                      w0, w1, w2, hl);
-    else t = seg_capsule64(P, d, q0, q1, q2, w0, w1, w2, hl);
+        t = seg_box64(__ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5), dl, q0, q1, q2,
+                      w0, w1, w2, el);
+    else if (kind == 2) t = seg_capsule64(P, dl, q0, q1, q2, w0, w1, w2, el);
+    else if (kind == 3) t = seg_torus64(P, dl, q0, q1, q2, w0, w1, w2, el);
+    else t = seg_cylinder64(P, dl, q0, q1, q2, w0, w1, w2, el);
     return s * t;
 }
 
+// The move bound: the bounding box's exit, the soft regions' isotropic
+// bound, then each listed primitive with margin e = m + delta/2 (its
+// regions' sum of k/4): 0 when |d| <= e, passed over when |d| - e cannot
+// lower the bound so far, else its ray bound.
 template <bool G>
 static __device__ __noinline__ double segment_bound64(const DevScene &S, double dsoft, double dbox, double px,
                                                       double py, double pz, double ux, double uy, double uz)
 {
     const double dh = 0.5 * S.delta;
-    double t = dsoft - dh;
+    double t = fmin(seg_box64(S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2], dbox, px, py, pz, ux, uy,
+                              uz, dh),
+                    dsoft - dh);
     for (int j = 0; j < S.nseg; ++j) {
         const int i = __ldg(S.seg_prims + j);
         const int kind = (*(S.pkind + i));
+        const double e = __ldg(S.seg_m64 + j) + dh;
         const double d = prim64<G>(S, kind, i, px, py, pz);
+        if (!(fabs(d) > e)) return 0.0;
+        if (fabs(d) - e >= t) continue;
         double b;
-        if (!(fabs(d) > dh)) {
-            b = 0.0;
-        } else if (kind == 0) {
-            b = seg_sphere64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, dh);
+        if (kind == 0) {
+            b = seg_sphere64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, e);
         } else if (kind == 1) {
             const double *P = S.p64 + 8 * i;
             b = seg_box64(__ldg(P), __ldg(P + 1), __ldg(P + 2), __ldg(P + 3), __ldg(P + 4), __ldg(P + 5), d, px,
-                          py, pz, ux, uy, uz, dh);
-        } else if (kind == 2) {
-            b = seg_capsule64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, dh);
-        } else if (G && (kind & kXformFlag)) {
-            b = seg_xprim64(S, kind & 0xf, i, d, px, py, pz, ux, uy, uz, dh);
+                          py, pz, ux, uy, uz, e);
+        } else if (!G || kind == 2) {
+            b = seg_capsule64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, e);
+        } else if (kind & kXformFlag) {
+            b = seg_xprim64(S, kind & 0xf, i, d, px, py, pz, ux, uy, uz, e);
+        } else if (kind == 3) {
+            b = seg_torus64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, e);
         } else {
-            b = fabs(d) - dh;            // tori and cylinders: isotropic
+            b = seg_cylinder64(S.p64 + 8 * i, d, px, py, pz, ux, uy, uz, e);
         }
         t = fmin(t, b);
     }
-    return fmin(t, seg_box64(S.bbc[0], S.bbc[1], S.bbc[2], S.bbh[0], S.bbh[1], S.bbh[2], dbox, px, py, pz, ux,
-                             uy, uz, dh));
+    return t;
 }
 
 // FP32 (mixed): the same bounds with reciprocal directions.
@@ -1018,13 +1072,51 @@ static __device__ __noinline__ float seg_capsule32(float4 A, float4 Bv, float d,
     return t > 0.f ? t : 0.f;
 }
 
-// FP32 placed sphere, box or capsule (frame without a domain operation).
+// FP32 capped cylinder (kind 4) and torus (kind 3) bounds, the FP64 rules
+// above; the tables hold (c, R or radius) and (tube radius or half height).
+static __device__ __noinline__ float seg_round32(int kind, const float4 *P, float d, float px, float py, float pz,
+                                                 float ux, float uy, float uz, float e)
+{
+    const float inf = __int_as_float(0x7f800000);
+    const float4 A = (*(P)), B = (*(P + 1));
+    if (kind == 3) {
+        if (d < 0.f) return -d - e;
+        const float R = A.w, rt = B.x + e;
+        const float ox = px - A.x, oy = py - A.y, oz = pz - A.z + rt;
+        const float iL2 = 1.0f / (4.f * rt * rt);
+        float a0, a1;
+        ray_cylinder32(ox, oy, oz, 0.f, 0.f, 2.f * rt, iL2, R + rt, ux, uy, uz, a0, a1);
+        float lo = fmaxf(a0, 0.f);
+        const float hi = a1;
+        if (!(lo <= hi)) return inf;
+        if (R - rt > 0.f) {
+            float b0, b1;
+            ray_cylinder32(ox, oy, oz, 0.f, 0.f, 2.f * rt, iL2, R - rt, ux, uy, uz, b0, b1);
+            if (b0 <= lo && lo < b1) lo = b1;
+            if (!(lo < hi)) return inf;
+        }
+        return fmaxf(lo, d - e);
+    }
+    const float g = d > 0.f ? e : -e;
+    const float rr = A.w + g, hh = B.x + g;
+    float t0, t1;
+    ray_cylinder32(px - A.x, py - A.y, pz - A.z + hh, 0.f, 0.f, 2.f * hh, 1.0f / (4.f * hh * hh), rr, ux, uy, uz,
+                   t0, t1);
+    if (d > 0.f) {
+        if (!(t0 <= t1) || t1 < 0.f) return inf;
+        return t0 > 0.f ? t0 : 0.f;
+    }
+    if (!(t0 <= t1)) return 0.f;
+    return t1 > 0.f ? t1 : 0.f;
+}
+
+// FP32 placed primitive (frame without a domain operation).
 static __device__ __noinline__ float seg_xprim32(const DevScene &S, int kind, int i, float d, float px, float py,
-                                                 float pz, float ux, float uy, float uz, float dh)
+                                                 float pz, float ux, float uy, float uz, float e)
 {
     const float4 *X = S.xf32 + kXf32 * i;
     const float4 R0 = __ldg(X), R1 = __ldg(X + 1), R2 = __ldg(X + 2), SC = __ldg(X + 3);
-    if ((int)SC.z != 0 || kind > 2) return fabsf(d) - dh;
+    if ((int)SC.z != 0) return fabsf(d) - e;
     const float vx = px - R0.w, vy = py - R1.w, vz = pz - R2.w;
     const float q0 = (R0.x * vx + R0.y * vy + R0.z * vz) * SC.y;
     const float q1 = (R1.x * vx + R1.y * vy + R1.z * vz) * SC.y;
@@ -1032,46 +1124,57 @@ static __device__ __noinline__ float seg_xprim32(const DevScene &S, int kind, in
     const float w0 = R0.x * ux + R0.y * uy + R0.z * uz;
     const float w1 = R1.x * ux + R1.y * uy + R1.z * uz;
     const float w2 = R2.x * ux + R2.y * uy + R2.z * uz;
-    const float hl = dh * SC.y;
+    const float dl = d * SC.y, el = e * SC.y;
     const float4 A = (*(S.p32 + 2 * i)), B = (*(S.p32 + 2 * i + 1));
     float t;
-    if (kind == 0) t = seg_sphere32(A, d, q0, q1, q2, w0, w1, w2, hl);
+    if (kind == 0) t = seg_sphere32(A, dl, q0, q1, q2, w0, w1, w2, el);
     else if (kind == 1)
-        t = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, q0, q1, q2, w0, w1, w2, 1.0f / w0, 1.0f / w1, 1.0f / w2, hl);
-    else t = seg_capsule32(A, B, d, q0, q1, q2, w0, w1, w2, hl);
+        t = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, dl, q0, q1, q2, w0, w1, w2, 1.0f / w0, 1.0f / w1, 1.0f / w2, el);
+    else if (kind == 2) t = seg_capsule32(A, B, dl, q0, q1, q2, w0, w1, w2, el);
+    else t = seg_round32(kind, S.p32 + 2 * i, dl, q0, q1, q2, w0, w1, w2, el);
     return SC.x * t;
 }
 
+// The move bound: the FP64 rule, with the culled region's distance (mixed)
+// among the soft regions' isotropic bounds.  Measured on the vessel tree: a
+// bound over the culled cell's candidates along the ray, or only the cell's
+// exit, cut the steps per packet (132 to 117-118) but made each packet
+// slower (cycles per packet +15 % with the cell's exit alone, +42 % with the
+// candidates); most of the loss came with the longer, more uneven moves'
+// tally (without a fluence grid the cell's exit alone cost 4 %).  The
+// isotropic bound is kept.
 template <bool G>
 static __device__ __noinline__ float segment_bound32(const DevScene &S, float dsoft, float dbox, float px,
                                                      float py, float pz, float ux, float uy, float uz)
 {
     const float dh = 0.5f * S.delta32;
     const float iux = 1.0f / ux, iuy = 1.0f / uy, iuz = 1.0f / uz;
-    float t = dsoft - dh;
+    float t = fminf(seg_box32(S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2], dbox, px, py,
+                              pz, ux, uy, uz, iux, iuy, iuz, dh),
+                    dsoft - dh);
     for (int j = 0; j < S.nseg; ++j) {
         const int i = __ldg(S.seg_prims + j);
         const int kind = (*(S.pkind + i));
+        const float e = __ldg(S.seg_m32 + j) + dh;
         const float d = prim32<G>(S, kind, i, px, py, pz);
+        if (!(fabsf(d) > e)) return 0.f;
+        if (fabsf(d) - e >= t) continue;
         float b;
-        if (!(fabsf(d) > dh)) {
-            b = 0.f;
-        } else if (kind == 0) {
-            b = seg_sphere32((*(S.p32 + 2 * i)), d, px, py, pz, ux, uy, uz, dh);
+        if (kind == 0) {
+            b = seg_sphere32((*(S.p32 + 2 * i)), d, px, py, pz, ux, uy, uz, e);
         } else if (kind == 1) {
             const float4 A = (*(S.p32 + 2 * i)), B = (*(S.p32 + 2 * i + 1));
-            b = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, px, py, pz, ux, uy, uz, iux, iuy, iuz, dh);
-        } else if (kind == 2) {
-            b = seg_capsule32((*(S.p32 + 2 * i)), (*(S.p32 + 2 * i + 1)), d, px, py, pz, ux, uy, uz, dh);
-        } else if (G && (kind & kXformFlag)) {
-            b = seg_xprim32(S, kind & 0xf, i, d, px, py, pz, ux, uy, uz, dh);
+            b = seg_box32(A.x, A.y, A.z, B.x, B.y, B.z, d, px, py, pz, ux, uy, uz, iux, iuy, iuz, e);
+        } else if (!G || kind == 2) {
+            b = seg_capsule32((*(S.p32 + 2 * i)), (*(S.p32 + 2 * i + 1)), d, px, py, pz, ux, uy, uz, e);
+        } else if (kind & kXformFlag) {
+            b = seg_xprim32(S, kind & 0xf, i, d, px, py, pz, ux, uy, uz, e);
         } else {
-            b = fabsf(d) - dh;
+            b = seg_round32(kind, S.p32 + 2 * i, d, px, py, pz, ux, uy, uz, e);
         }
         t = fminf(t, b);
     }
-    return fminf(t, seg_box32(S.bbc32[0], S.bbc32[1], S.bbc32[2], S.bbh32[0], S.bbh32[1], S.bbh32[2], dbox, px,
-                              py, pz, ux, uy, uz, iux, iuy, iuz, dh));
+    return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -1194,13 +1297,13 @@ __device__ __forceinline__ void tally32(const DevScene &S, long long *flu, float
     const float inf = __int_as_float(0x7f800000);
     const float lx = S.g_lo32[0], ly = S.g_lo32[1], lz = S.g_lo32[2];
     const float dx = S.g_dl32[0], dy = S.g_dl32[1], dz = S.g_dl32[2];
-    int ix = min(max(__float2int_rd((px + tin * ux - lx) * S.g_idl32[0]), 0), nx - 1);
-    int iy = min(max(__float2int_rd((py + tin * uy - ly) * S.g_idl32[1]), 0), ny - 1);
-    int iz = min(max(__float2int_rd((pz + tin * uz - lz) * S.g_idl32[2]), 0), nz - 1);
+    int ix = min(max(__float2int_rd((__fmaf_rn(tin, ux, px) - lx) * S.g_idl32[0]), 0), nx - 1);
+    int iy = min(max(__float2int_rd((__fmaf_rn(tin, uy, py) - ly) * S.g_idl32[1]), 0), ny - 1);
+    int iz = min(max(__float2int_rd((__fmaf_rn(tin, uz, pz) - lz) * S.g_idl32[2]), 0), nz - 1);
     const int sx = ux > 0.f ? 1 : -1, sy = uy > 0.f ? 1 : -1, sz = uz > 0.f ? 1 : -1;
-    float tx = ux != 0.f ? ((lx + (float)(ix + (sx > 0)) * dx) - px) * iux : inf;
-    float ty = uy != 0.f ? ((ly + (float)(iy + (sy > 0)) * dy) - py) * iuy : inf;
-    float tz = uz != 0.f ? ((lz + (float)(iz + (sz > 0)) * dz) - pz) * iuz : inf;
+    float tx = ux != 0.f ? (__fmaf_rn((float)(ix + (sx > 0)), dx, lx) - px) * iux : inf;
+    float ty = uy != 0.f ? (__fmaf_rn((float)(iy + (sy > 0)), dy, ly) - py) * iuy : inf;
+    float tz = uz != 0.f ? (__fmaf_rn((float)(iz + (sz > 0)), dz, lz) - pz) * iuz : inf;
     const float tdx = ux != 0.f ? dx * fabsf(iux) : inf;
     const float tdy = uy != 0.f ? dy * fabsf(iuy) : inf;
     const float tdz = uz != 0.f ? dz * fabsf(iuz) : inf;

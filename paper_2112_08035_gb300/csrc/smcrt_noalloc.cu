@@ -154,8 +154,11 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     const size_t o_r64 = take(sizeof(double) * 8 * nr);
     const size_t o_r32 = take(sizeof(float4) * 2 * nr);
     int32_t segp[kMaxPrims];
-    const int nseg = sc->stepping == SMCRT_STEP_SEGMENT ? hard_region_prims(sc, segp) : 0;
+    double segm[kMaxPrims];
+    const int nseg = sc->stepping == SMCRT_STEP_SEGMENT ? seg_entries(sc, segp, segm) : 0;
     const size_t o_seg = take(sizeof(int32_t) * nseg);
+    const size_t o_segm64 = take(sizeof(double) * nseg);
+    const size_t o_segm32 = take(sizeof(float) * nseg);
     const bool has_xf = sc->nxforms > 0;
     const size_t o_xf64 = take(has_xf ? sizeof(double) * kXf64 * np : 0);
     const size_t o_xf32 = take(has_xf ? sizeof(float4) * kXf32 * np : 0);
@@ -186,7 +189,12 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     std::memcpy(img + o_ins, ins, sizeof(Instr) * ni);
     std::memcpy(img + o_k64, k64, sizeof(double) * ni);
     std::memcpy(img + o_rr, rr, sizeof(int2) * nr);
-    if (nseg > 0) std::memcpy(img + o_seg, segp, sizeof(int32_t) * nseg);
+    if (nseg > 0) {
+        std::memcpy(img + o_seg, segp, sizeof(int32_t) * nseg);
+        std::memcpy(img + o_segm64, segm, sizeof(double) * nseg);
+        float *m32 = (float *)(img + o_segm32);
+        for (int j = 0; j < nseg; ++j) m32[j] = (float)segm[j];
+    }
 
     unsigned char *base = dev_base + kImageOff;   // device addresses of the tables
     DevScene H;
@@ -218,6 +226,8 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
     H.stepping = sc->stepping;
     H.nseg = nseg;
     H.seg_prims = nseg > 0 ? (const int32_t *)(base + o_seg) : nullptr;
+    H.seg_m64 = nseg > 0 ? (const double *)(base + o_segm64) : nullptr;
+    H.seg_m32 = nseg > 0 ? (const float *)(base + o_segm32) : nullptr;
     H.xf64 = has_xf ? (const double *)(base + o_xf64) : nullptr;
     H.xf32 = has_xf ? (const float4 *)(base + o_xf32) : nullptr;
     for (int i = 0; i < np; ++i) H.general = H.general || !plain_prim(sc->prims[i]);

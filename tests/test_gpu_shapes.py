@@ -68,7 +68,51 @@ SHAPES = {
     "repeat": W.Prim(W.SPHERE, (0.0, 0.0, 0.0, 0.1), W.Xform(t=(0.0, 0.0, -0.6), op=W.REPEAT,
                                                              a=(0.3, 0.3, 0.0, 2.0))),
     "cylinder_plain": W.Prim(W.CYLINDER, (0.0, 0.0, -1.0, 0.4, 0.3)),
+    "torus_plain": W.Prim(W.TORUS, (0.1, 0.0, -1.0, 0.5, 0.2)),
 }
+
+
+def _smooth_blob(n=400, precision="fp64"):
+    """Spheres and capsules joined by smooth unions, one sphere given twice
+    (the fold then reaches past k/4 below the plain union), in a tissue
+    block lit from above.  Under segment stepping the region is bounded
+    along rays with a margin of k/4 per smooth union."""
+    prims = (W.Prim(W.BOX, (0.0, 0.0, -1.0, 1.5, 1.5, 1.0)),
+             W.Prim(W.SPHERE, (0.0, 0.0, -0.8, 0.35)), W.Prim(W.SPHERE, (0.3, 0.1, -0.9, 0.3)),
+             W.Prim(W.SPHERE, (0.0, 0.0, -0.8, 0.35)),
+             W.Prim(W.CAPSULE, (-0.6, -0.2, -1.2, 0.5, 0.3, -1.3, 0.12)),
+             W.Prim(W.CAPSULE, (0.0, -0.7, -0.6, 0.0, 0.7, -0.7, 0.1)))
+    prog = (W.Node(W.PRIM, 1), W.Node(W.PRIM, 2), W.Node(W.SMOOTH_UNION, -1, 0.15), W.Node(W.PRIM, 3),
+            W.Node(W.SMOOTH_UNION, -1, 0.15), W.Node(W.PRIM, 4), W.Node(W.SMOOTH_UNION, -1, 0.1),
+            W.Node(W.PRIM, 5), W.Node(W.UNION))
+    regions = (W.Region(W.prim_program([0]), 0.3, 15.0, 0.8, 1.37), W.Region(prog, 1.0, 30.0, 0.9, 1.45))
+    scene = W.Scene(prims, regions, 1.0, (-1.6, -1.6, -2.1), (1.6, 1.6, 0.2))
+    return W.Workload("smooth_blob", scene, W.Source(W.DISC, (0.0, 0.0, 0.1), (0.0, 0.0, -1.0), 0.8),
+                      W.Grid((-1.5, -1.5, -2.0), (1.5, 1.5, 0.0), (16, 16, 16)), n, 9, precision)
+
+
+@pytest.mark.parametrize("stepping", [W.SPHERE_TRACING, W.SEGMENT])
+def test_fp64_bitexact_smooth_fold(ctx, stepping):
+    wl = _smooth_blob().with_stepping(stepping)
+    fo, to, ro = O.run(wl, records=True)
+    fg, tg, rg = run_gpu(ctx, wl, "fp64", records=True)
+    for k in ("R", "T", "A", "killed", "gain", "packets", "scatters", "steps"):
+        assert tg[k] == to[k], (k, tg[k], to[k])
+    assert np.array_equal(fg, fo)
+    for f in ("R", "T", "A", "killed", "gain", "scatters", "steps"):
+        assert np.array_equal(rg[f], ro[f]), f
+
+
+def test_mixed_smooth_fold_matches_oracle(ctx):
+    wl = _smooth_blob(precision="mixed")
+    _, _, ro = O.run(wl.with_packets(6000), records=True)
+    _, tg, rg = run_gpu(ctx, wl.with_packets(200_000).with_stepping(W.SEGMENT), "mixed", records=True,
+                        id_begin=5_000_000)
+    for key in ("R", "T", "A"):
+        assert abs(_z(rg, ro, key)) < 4.0, (key, _z(rg, ro, key))
+    bal = (rg["R"] + rg["T"] + rg["A"] + rg["killed"] - rg["gain"]) / FX
+    assert np.all(np.abs(bal - 1.0) < 1e-4)
+    assert tg["max_steps_hit"] == 0
 
 
 @pytest.mark.parametrize("stepping", [W.SPHERE_TRACING, W.SEGMENT])
