@@ -858,15 +858,27 @@ def main():
         # ---- served mix (config 4): Poisson arrivals at 80% of capacity -------
         if args.serve_jobs > 0:
             log("serving leg")
-            # capacity of the server on this mix: all jobs of a prefix at once
+            # capacity of the server on this mix: all jobs of a prefix at once;
+            # beside it the same jobs run one after another through smcrt_run,
+            # each tallying into a device grid as the served jobs do
             cap_jobs = W.served_mix(min(40, args.serve_jobs), 4, stepping=args.stepping)
+            t0 = time.perf_counter()
+            for j in cap_jobs:
+                g = j.grid
+                ctx.run(j, "mixed", out=torch.zeros((g.n[2], g.n[1], g.n[0]), dtype=torch.int64, device="cuda"))
+            torch.cuda.synchronize()
+            seq_s = time.perf_counter() - t0
             t0 = time.perf_counter()
             jids = [ctx.submit(j, "mixed") for j in cap_jobs]
             for jid in jids:
                 ctx.wait(jid, -1.0, fluence=False)
-            cap = sum(j.npackets for j in cap_jobs) / (time.perf_counter() - t0)
+            served_s = time.perf_counter() - t0
+            cap = sum(j.npackets for j in cap_jobs) / served_s
             out["serving"] = served_mix(ctx, args.serve_jobs, capacity_pps=cap, stepping=args.stepping)
             out["serving"]["capacity_pps"] = cap
+            out["serving"]["batch"] = {"jobs": len(cap_jobs), "packets": sum(j.npackets for j in cap_jobs),
+                                       "served_s": served_s, "sequential_s": seq_s,
+                                       "sequential": "smcrt_run per job, device fluence grid"}
             out["serving"]["stepping"] = args.stepping
     plan.close()
     print(json.dumps(out), flush=True)

@@ -721,11 +721,19 @@ constexpr int kRoundsInFlight = 2;
 constexpr double kRoundSeconds = 0.008;   // target device time of one round
 constexpr double kParkSeconds = 0.004;    // device time a packet may run per round before it is parked
 constexpr double kDrainSeconds = 0.0005;  // ... once its warp has no more work, in rounds with new ids
-constexpr unsigned kDeferCap = 65536;     // parked packets per list and job
+constexpr double kTailSeconds = 0.05;     // ... in rounds of parked packets only, with no job waiting
+// Parked packets per list and job: at least one per lane of the served
+// kernels' launches (the tuned mixed shapes hold up to about 1e5 lanes on
+// 152 SMs).  At a round's end nearly every lane holds a packet younger than
+// its lifetime (1.5 ms on the layered slab under full load); a packet that
+// finds the list full keeps running, and the round then waits for the
+// longest of them (measured with 65,536 entries: 11 ms rounds for 8 ms of
+// work, the list full every round).
+constexpr unsigned kDeferCap = 131072;
 
 size_t job_bytes(const smcrt_grid &g)
 {
-    return (size_t)g.n[0] * g.n[1] * g.n[2] * 8 + 65536;
+    return (size_t)g.n[0] * g.n[1] * g.n[2] * 8 + 65536 + 2 * sizeof(DeferState) * (size_t)kDeferCap;
 }
 
 void free_job_device(Job &j, cudaStream_t st)
@@ -818,6 +826,7 @@ void scheduler(smcrt_ctx *ctx)
     auto round_cycles = [&] { return (double)blocks_m * (threads_m / 32) * clk_khz * 1e3 * kRoundSeconds; };
     const long long park_cycles = (long long)(clk_khz * 1e3 * kParkSeconds);
     const long long drain_cycles = (long long)(clk_khz * 1e3 * kDrainSeconds);
+    const long long tail_cycles = (long long)(clk_khz * 1e3 * kTailSeconds);
     // SMCRT_FAULT_BAD_JOB=<job id>: that job's round-table entry gets no
     // scene, which the kernels report as a bad job (host-side injection for
     // the status tests; no GPU fault is involved).
@@ -886,11 +895,14 @@ void scheduler(smcrt_ctx *ctx)
     if (setup_rc == SMCRT_OK) setup_rc = capture();
 
     // Timing trials of the served mixed kernel on one job's scene (scratch
-    // tallies, ids from 0 with the job's seed): register variant x threads x
-    // resident blocks, as smcrt_plan_autotune does for a plan.  Results do
-    // not depend on the choice (every variant computes the same bits).
+    // tallies, ids from 0 with the job's seed, whatever the job's own size):
+    // register variant x threads x resident blocks, as smcrt_plan_autotune
+    // does for a plan.  A trial gives every lane a few packets (4e5 packets,
+    // about 8 ms on the layered slab), so it times throughput rather than
+    // one packet's lifetime.  Results do not depend on the choice (every
+    // variant computes the same bits).
     auto tune_served = [&](const Job &j) {
-        const uint64_t trial = std::min<uint64_t>(j.npackets, 50000);
+        const uint64_t trial = 400000;
         const size_t cells = (size_t)j.grid.n[0] * j.grid.n[1] * j.grid.n[2];
         void *flu = nullptr, *tot = nullptr, *tab = nullptr, *tst = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1138,6 +1150,17 @@ void scheduler(smcrt_ctx *ctx)
             if (j->cursor < j->npackets) ++nfresh;
         }
         const double dflt = nk ? known / nk : 2.0e5;
+        // A round of parked packets only (every id claimed), with no job
+        // waiting for admission: its packets are the last of their jobs, and
+        // parking them again after 4 ms only repeats near-empty rounds
+        // (measured: fifteen 4 ms rounds of a few hundred packets at the end
+        // of a 40-job batch), so they run up to 50 ms.
+        bool waiting = false;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            waiting = !ctx->queue.empty();
+        }
+        const long long budget = nfresh == 0 && !waiting ? tail_cycles : park_cycles;
         const double share = round_cycles() / (double)std::max(1, nfresh);
         int nm = 0, nd = 0;
         bool general = false;
@@ -1157,10 +1180,10 @@ void scheduler(smcrt_ctx *ctx)
             w.records = nullptr;
             w.scene = j->id == bad_job ? nullptr : j->plan->dscene;
             w.cancelled = 0;
-            w.park_cycles = park_cycles;
+            w.park_cycles = budget;
             // a round with new ids ends soon after they run out; a round of
             // parked packets only lets them run the full budget
-            w.drain_cycles = nfresh > 0 ? drain_cycles : park_cycles;
+            w.drain_cycles = nfresh > 0 ? drain_cycles : budget;
             w.jstat = d_jstat + j->slot;
             w.defer = j->ddefer;
             w.defer_in = (int32_t)(issued & 1);
