@@ -567,44 +567,11 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
             }
             if (__all_sync(SMCRT_FULL, retired)) break;
         } else {
-            unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            // plan launches: new ids only (parking belongs to served rounds,
+            // which run the multi-job kernel; leaving it out of this one
+            // keeps its loop smaller)
+            const unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
             const volatile JobConst *const jc = jc0;
-            JobDefer *const dfr = (JobDefer *)jc->dfr;
-            const int din = jc->din;
-            if (SMCRT_RARE(need && dfr != nullptr)) {
-                const int leader = __ffs(need) - 1;
-                unsigned base = 0u, avail = 0u;
-                if (lane == leader) {
-                    // the counter also counts packets that found the list full
-                    // (they kept running): only the first `cap` entries exist
-                    avail = min(*(volatile unsigned *)&dfr->count[din], dfr->cap);
-                    base = atomicAdd(&dfr->cursor[din], (unsigned)__popc(need));
-                }
-                base = __shfl_sync(SMCRT_FULL, base, leader);
-                avail = __shfl_sync(SMCRT_FULL, avail, leader);
-                if (!alive && !retired) {
-                    const unsigned k = base + (unsigned)__popc(need & ((1u << lane) - 1u));
-                    if (k < avail) {
-                        const DeferState &d = dfr->buf[din][k];
-                        px = (float)d.p[0]; py = (float)d.p[1]; pz = (float)d.p[2];
-                        ux = (float)d.u[0]; uy = (float)d.u[1]; uz = (float)d.u[2];
-                        w = (float)d.w; tau = (float)d.tau;
-                        pA = d.pA; pG = d.pG;
-                        id_lo = d.id_lo; id_hi = d.id_hi; event = d.event;
-                        nsteps = (int)d.nsteps; pscat = d.pscat;
-                        phase = kTrace;
-                        cs = __uint_as_float(d.pad[0]);
-                        pend = __uint_as_float(d.pad[1]);
-                        if (cs >= 0.f) {           // parked in a crawl: p holds the anchor
-                            qx = px; qy = py; qz = pz;
-                            px = __fmaf_rn(cs, ux, qx); py = __fmaf_rn(cs, uy, qy); pz = __fmaf_rn(cs, uz, qz);
-                        }
-                        t_acq = (uint32_t)clock();
-                        alive = true;
-                    }
-                }
-                need = __ballot_sync(SMCRT_FULL, !alive && !retired);
-            }
             const bool want = !alive && !retired;
             if (need) {
                 const int leader = __ffs(need) - 1;
@@ -877,11 +844,11 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                 recs[id - jc->begin] = r;
             }
         }
-        // ---- park a straggler at a trace boundary (serving rounds only).  A
+        // ---- park a straggler at a trace boundary (served rounds).  A
         // packet in a crawl is parked as its anchor and crawl length, from
         // which the resume recomputes the same position.
-        if (SMCRT_RARE(alive && phase == kTrace && jc->budget > 0u &&
-                       (uint32_t)clock() - t_acq > (MULTI && drained ? jc->drain : jc->budget))) {
+        if (MULTI && SMCRT_RARE(alive && phase == kTrace && jc->budget > 0u &&
+                                (uint32_t)clock() - t_acq > (drained ? jc->drain : jc->budget))) {
             JobDefer *const dfr = (JobDefer *)jc->dfr;
             const int din = jc->din;
             const unsigned k = atomicAdd(&dfr->count[1 - din], 1u);
