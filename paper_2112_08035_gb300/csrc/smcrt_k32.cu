@@ -835,8 +835,9 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                 npieces = 0u;
                 wadd(wa, kBusy, (long long)(((uint32_t)clock() - t_acq) >> 5));
             }
+            // per-packet records belong to plan launches (served jobs have none)
             smcrt_packet_record *const recs = (smcrt_packet_record *)jc->recs;
-            if (recs) {
+            if (!MULTI && recs) {
                 smcrt_packet_record r;
                 r.R = fin_R; r.T = fin_T; r.A = pA; r.killed = fin_K; r.gain = pG;
                 r.scatters = pscat; r.steps = nsteps; r.reserved = 0;
