@@ -862,6 +862,9 @@ def main():
             # beside it the same jobs run one after another through smcrt_run,
             # each tallying into a device grid as the served jobs do
             cap_jobs = W.served_mix(min(40, args.serve_jobs), 4, stepping=args.stepping)
+            # one small job first: the server's one-time launch-shape trials
+            # (on the first mixed job it serves) stay out of the timed batch
+            ctx.wait(ctx.submit(cap_jobs[0].with_packets(20_000), "mixed"), -1.0, fluence=False)
             t0 = time.perf_counter()
             for j in cap_jobs:
                 g = j.grid
