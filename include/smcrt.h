@@ -142,15 +142,19 @@ enum smcrt_stepping {
     SMCRT_STEP_SPHERE_TRACING = 0,
     /* Segment stepping (Sec. 5 names segment tracing for packets moving
      * nearly parallel to a surface): move max(d_min - delta/2, B), where B
-     * bounds the move along the packet's own direction -- for every box,
-     * sphere and capsule of a region built by hard CSG (union,
-     * intersection, subtraction), also when placed by a frame without a
-     * domain operation, the distance along the ray to its surface offset by
-     * delta/2; for regions with a smooth union, for tori, cylinders and
-     * domain operations |d| - delta/2 (in mixed precision also
-     * for a union of 16 or more primitives, which is evaluated through a
-     * grid of per-cell candidate lists); for the bounding box
-     * its exit distance less delta/2.  The
+     * bounds the move along the packet's own direction.  Each primitive of
+     * a region with at most eight smooth unions takes the margin
+     * e = M + delta/2, M the sum of k/4 over the smooth unions of the
+     * regions that use it (0 for hard CSG: union, intersection,
+     * subtraction); its bound is the distance along the ray until |d| can
+     * reach e: spheres, boxes, capsules and capped cylinders grown by e
+     * from outside and shrunk by e from inside, tori from outside (through
+     * the annular slab that holds the grown tube), the same shapes placed
+     * by a frame without a domain operation; |d| - e inside a torus and
+     * for domain operations.  Regions with more than eight smooth unions
+     * take |d| - delta/2 (in mixed precision so does a union of 16 or more
+     * primitives, which is evaluated through a grid of per-cell candidate
+     * lists); the bounding box takes its exit distance less delta/2.  The
      * move stops delta/2 short of the first surface it would reach, and the
      * interface handling is unchanged.  Same transport, fewer steps. */
     SMCRT_STEP_SEGMENT = 1
