@@ -310,6 +310,7 @@ struct JobSlot {
     DevScene S;
     WarpAcc acc;
     JobConst jc;
+    int rdone;               // served rounds: this job's parked list is used up for the round
 };
 struct WarpShared {          // plan launches: one job at a time, tables optionally staged
     JobSlot slot;
@@ -413,7 +414,10 @@ __device__ __forceinline__ void multi_stage(JobSlot *sl, JobWork *J, int lane)
     const long long *s8 = reinterpret_cast<const long long *>(J->scene);
     long long *d8 = reinterpret_cast<long long *>(&sl->S);
     for (int i = lane; i < (int)(sizeof(DevScene) / 8); i += 32) d8[i] = s8[i];
-    if (lane == 0) jobconst_fill(&sl->jc, J);
+    if (lane == 0) {
+        jobconst_fill(&sl->jc, J);
+        sl->rdone = 0;
+    }
     wacc_clear(&sl->acc, lane);
     __syncwarp();
 }
@@ -488,7 +492,7 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                 JobSlot *const sf = slots + feed;
                 JobWork *const Jf = jobs + (feed ? sj1 : sj0);
                 JobDefer *const dfr = (JobDefer *)sf->jc.dfr;
-                if (dfr != nullptr) {          // the feed job's parked packets
+                if (dfr != nullptr && !*(volatile int *)&sf->rdone) {   // the feed job's parked packets
                     const int din = sf->jc.din;
                     const int leader = __ffs(need) - 1;
                     unsigned base = 0u, avail = 0u;
@@ -498,6 +502,12 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                     }
                     base = __shfl_sync(SMCRT_FULL, base, leader);
                     avail = __shfl_sync(SMCRT_FULL, avail, leader);
+                    // the list only shrinks during a round (new parks go to the
+                    // other one): once the cursor passes its count, stop asking
+                    if (base + (unsigned)__popc(need) >= avail) {
+                        if (lane == 0) *(volatile int *)&sf->rdone = 1;
+                        __syncwarp();
+                    }
                     if (!alive && !retired) {
                         const unsigned k = base + (unsigned)__popc(need & ((1u << lane) - 1u));
                         if (k < avail) {
