@@ -311,6 +311,7 @@ struct JobSlot {
     WarpAcc acc;
     JobConst jc;
     int rdone;               // served rounds: this job's parked list is used up for the round
+    int idone;               // ... and its ids are all claimed
 };
 struct WarpShared {          // plan launches: one job at a time, tables optionally staged
     JobSlot slot;
@@ -417,6 +418,7 @@ __device__ __forceinline__ void multi_stage(JobSlot *sl, JobWork *J, int lane)
     if (lane == 0) {
         jobconst_fill(&sl->jc, J);
         sl->rdone = 0;
+        sl->idone = 0;
     }
     wacc_clear(&sl->acc, lane);
     __syncwarp();
@@ -455,6 +457,10 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
     // full one), so a round is not held open by a few long-lived packets
     // while the rest of the GPU idles; they resume next round among new work.
     bool drained = false;
+    // served rounds: a search found no job with work; within a round none
+    // appears later (ids only get claimed, parked lists only get resumed),
+    // so idle lanes retire without asking again
+    bool nomore = false;
     if (MULTI) {
         const int nj = multi_find<G>(jobs, njobs, scan, -1, skip, status, lane);
         if (nj < 0) return false;
@@ -488,6 +494,10 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
         // ---- 1. refill: this job's parked packets first, then new ids
         if (MULTI) {
             unsigned need = __ballot_sync(SMCRT_FULL, !alive && !retired);
+            if (nomore) {
+                if (!alive) retired = true;
+                need = 0u;
+            }
             for (int pass = 0; need != 0u && pass < 4; ++pass) {
                 JobSlot *const sf = slots + feed;
                 JobWork *const Jf = jobs + (feed ? sj1 : sj0);
@@ -532,7 +542,7 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                     }
                     need = __ballot_sync(SMCRT_FULL, !alive && !retired);
                 }
-                if (need != 0u) {              // the feed job's new ids
+                if (need != 0u && !*(volatile int *)&sf->idone) {   // the feed job's new ids
                     const int leader = __ffs(need) - 1;
                     unsigned long long base = 0;
                     if (lane == leader)
@@ -540,6 +550,10 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                                    ? ~0ull
                                    : atomicAdd(&Jf->next, (unsigned long long)__popc(need));
                     base = __shfl_sync(SMCRT_FULL, base, leader);
+                    if (base == ~0ull || base + (unsigned long long)__popc(need) >= sf->jc.end) {
+                        if (lane == 0) *(volatile int *)&sf->idone = 1;
+                        __syncwarp();
+                    }
                     if (!alive && !retired) {
                         const unsigned long long id =
                             base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
@@ -568,6 +582,7 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                 if (nj < 0) {                  // no job has work left: idle lanes retire
                     if (!alive) retired = true;
                     drained = true;
+                    nomore = true;
                     break;
                 }
                 multi_stage(slots + o, jobs + nj, lane);
