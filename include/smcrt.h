@@ -149,9 +149,10 @@ enum smcrt_stepping {
      * subtraction); its bound is the distance along the ray until |d| can
      * reach e: spheres, boxes, capsules and capped cylinders grown by e
      * from outside and shrunk by e from inside, tori from outside (through
-     * the annular slab that holds the grown tube), the same shapes placed
-     * by a frame without a domain operation; |d| - e inside a torus and
-     * for domain operations.  Regions with more than eight smooth unions
+     * the annular slab that holds the grown tube) and from inside (through
+     * the ball of radius r - e about the nearest point of the core circle),
+     * the same shapes placed by a frame without a domain operation;
+     * |d| - e for domain operations.  Regions with more than eight smooth unions
      * take |d| - delta/2 (in mixed precision so does a union of 16 or more
      * primitives, which is evaluated through a grid of per-cell candidate
      * lists); the bounding box takes its exit distance less delta/2.  The

@@ -672,7 +672,8 @@ static void launch(const or_source *src, double p[3], double u[3], double *tau, 
  *     rounded one); inside, the exit of the shape shrunk by e (exactly the
  *     set d_i < -e of these convex shapes);
  *   - torus from outside: the entry of the annular slab that holds the tube
- *     grown by e, and at least d_i - e; from inside, d_i's own |d_i| - e;
+ *     grown by e, and at least d_i - e; from inside, the exit of the ball of
+ *     radius r - e about the nearest point of the core circle;
  *   - the same shapes placed by a frame without a domain operation, in the
  *     frame's coordinates; domain operations: |d_i| - e.
  * On [0, t) every primitive keeps |d_i| > e, so no region's sign changes and
@@ -839,10 +840,19 @@ static double segment_cylinder(const double *q, double d, const double p[3], con
 /* Torus about z (major radius q[3], tube q[4]) from outside: the tube grown
  * by e lies in the annular slab R - r' <= rho <= R + r', |z - c_z| <= r'
  * (r' = r + e); the ray's first point in that slab, and never less than
- * d - e.  From inside the tube: |d| - e. */
+ * d - e.  From inside: the tube shrunk by e holds the ball of radius r - e
+ * about the point of the core circle nearest p (which that ball contains,
+ * at depth |d| - e), so the ray's exit from the ball bounds the move
+ * (p on the axis: |d| - e). */
 static double segment_torus(const double *q, double d, const double p[3], const double u[3], double e)
 {
-    if (d < 0.0) return -d - e;
+    if (d < 0.0) {
+        double dx = p[0] - q[0], dy = p[1] - q[1];
+        double rho = sqrt(dx * dx + dy * dy);
+        if (!(rho > 0.0)) return -d - e;
+        double ball[4] = {q[0] + q[3] * dx / rho, q[1] + q[3] * dy / rho, q[2], q[4]};
+        return segment_sphere(ball, d, p, u, e);
+    }
     double R = q[3], rt = q[4] + e;
     double ox = p[0] - q[0], oy = p[1] - q[1], oz = p[2] - q[2] + rt;
     double a0, a1;

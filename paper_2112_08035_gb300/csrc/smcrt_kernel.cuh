@@ -677,8 +677,9 @@ __device__ __forceinline__ double surface64(const DevScene &S, int r, double x, 
 // smooth unions (a region's surface lies where some primitive has |d| <= m):
 // spheres, boxes, capsules and capped cylinders grown by e from outside and
 // shrunk by e from inside, tori from outside through the annular slab that
-// holds the grown tube, the same shapes placed by a frame without a domain
-// operation, |d| - e otherwise; |d| - delta/2 for soft regions (dsoft); the
+// holds the grown tube and from inside through a ball the shrunk tube holds,
+// the same shapes placed by a frame without a domain operation, |d| - e
+// otherwise; |d| - delta/2 for soft regions (dsoft); the
 // exit of the bounding box shrunk by delta/2.  The caller moves
 // max(d_min - delta/2, bound).  FP64: the reference's operations in its
 // order.
@@ -846,12 +847,29 @@ static __device__ __noinline__ double seg_cylinder64(const double *P, double d, 
 
 // Torus about z (major radius P[3], tube P[4]) from outside: the first point
 // of the ray in the annular slab that holds the tube grown by e, and never
-// less than d - e; from inside the tube, |d| - e.
+// less than d - e.  From inside the tube: the exit of the ball of radius
+// r - e about the point of the core circle nearest p, which the tube shrunk
+// by e holds (on the axis: |d| - e).
 static __device__ __noinline__ double seg_torus64(const double *P, double d, double px, double py, double pz,
                                                   double ux, double uy, double uz, double e)
 {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    if (d < 0.0) return -d - e;
+    if (d < 0.0) {
+        const double dx = px - __ldg(P), dy = py - __ldg(P + 1);
+        const double rho = sqrt(dx * dx + dy * dy);
+        if (!(rho > 0.0)) return -d - e;
+        const double cx = __ldg(P) + __ldg(P + 3) * dx / rho, cy = __ldg(P + 1) + __ldg(P + 3) * dy / rho;
+        const double rr = __ldg(P + 4) - e;
+        const double ox = px - cx, oy = py - cy, oz = pz - __ldg(P + 2);
+        const double b = ox * ux + oy * uy + oz * uz;
+        const double cc = ox * ox + oy * oy + oz * oz - rr * rr;
+        const double disc = b * b - cc;
+        if (disc < 0.0) return 0.0;
+        double t;
+        if (b > 0.0) t = -cc / (b + sqrt(disc));
+        else t = sqrt(disc) - b;
+        return t > 0.0 ? t : 0.0;
+    }
     const double R = __ldg(P + 3), rt = __ldg(P + 4) + e;
     const double ox = px - __ldg(P), oy = py - __ldg(P + 1), oz = pz - __ldg(P + 2) + rt;
     double a0, a1;
@@ -1080,7 +1098,20 @@ static __device__ __noinline__ float seg_round32(int kind, const float4 *P, floa
     const float inf = __int_as_float(0x7f800000);
     const float4 A = (*(P)), B = (*(P + 1));
     if (kind == 3) {
-        if (d < 0.f) return -d - e;
+        if (d < 0.f) {                   // inside: the ball about the nearest core-circle point
+            const float dx = px - A.x, dy = py - A.y;
+            const float rho = sqrtf(dx * dx + dy * dy);
+            if (!(rho > 0.f)) return -d - e;
+            const float cx = A.x + A.w * dx / rho, cy = A.y + A.w * dy / rho;
+            const float rr = B.x - e;
+            const float ox = px - cx, oy = py - cy, oz = pz - A.z;
+            const float b = ox * ux + oy * uy + oz * uz;
+            const float cc = ox * ox + oy * oy + oz * oz - rr * rr;
+            const float disc = b * b - cc;
+            if (disc < 0.f) return 0.f;
+            const float t = b > 0.f ? -cc / (b + sqrtf(disc)) : sqrtf(disc) - b;
+            return t > 0.f ? t : 0.f;
+        }
         const float R = A.w, rt = B.x + e;
         const float ox = px - A.x, oy = py - A.y, oz = pz - A.z + rt;
         const float iL2 = 1.0f / (4.f * rt * rt);

@@ -80,7 +80,10 @@ MUTANTS = [
     ("segment_cylinder_exit", "    return t1 > 0.0 ? t1 : 0.0;\n}\n\n/* Torus", "    return t0 > 0.0 ? t0 : 0.0;\n}\n\n/* Torus"),
     ("segment_torus_growth", "double R = q[3], rt = q[4] + e;", "double R = q[3], rt = q[4];"),
     ("segment_torus_hole", "if (b0 <= lo && lo < b1) lo = b1;", "if (0) lo = b1;"),
-    ("segment_torus_inside", "if (d < 0.0) return -d - e;", "if (d < 0.0) return -d;"),
+    ("segment_torus_inside_center", "double ball[4] = {q[0] + q[3] * dx / rho, q[1] + q[3] * dy / rho, q[2], q[4]};",
+     "double ball[4] = {q[0] + q[3] * dx, q[1] + q[3] * dy, q[2], q[4]};"),
+    ("segment_torus_inside_radius", "double ball[4] = {q[0] + q[3] * dx / rho, q[1] + q[3] * dy / rho, q[2], q[4]};",
+     "double ball[4] = {q[0] + q[3] * dx / rho, q[1] + q[3] * dy / rho, q[2], q[3]};"),
     ("segment_xprim_direction", "w[0] = X->rot[0] * u[0] + X->rot[3] * u[1] + X->rot[6] * u[2];",
      "w[0] = X->rot[0] * u[0] + X->rot[1] * u[1] + X->rot[2] * u[2];"),
 ]

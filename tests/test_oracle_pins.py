@@ -1163,8 +1163,16 @@ def test_segment_step_exact_for_cylinders_and_tori():
     assert math.isclose(O.segment_step(tor, (0.5, 0.0, 1.0), down), 1.0 - 0.15 - d / 2, rel_tol=1e-12)
     # down the axis through the hole: only the bounding box bounds the move
     assert math.isclose(O.segment_step(tor, (0.0, 0.0, 1.0), down), 6.0 - d / 2, rel_tol=1e-12)
-    # inside the tube: the isotropic bound
-    assert math.isclose(O.segment_step(tor, (0.5, 0.0, 0.05), np.array([1.0, 0.0, 0.0])), 0.1 - d / 2,
+    # inside the tube: the exit of the ball of radius r - delta/2 about the
+    # nearest point of the core circle, longer than the isotropic 0.1 - delta/2
+    # when the ray runs across the tube
+    rb = 0.15 - d / 2
+    for u in (np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])):
+        t = O.segment_step(tor, (0.5, 0.0, 0.05), u)
+        assert math.isclose(t, math.sqrt(rb * rb - 0.05 * 0.05), rel_tol=1e-12)
+        _brute_force_move(tor, (0.5, 0.0, 0.05), u, t)
+    # straight down through the core circle: the ball's far side
+    assert math.isclose(O.segment_step(tor, (0.5, 0.0, 0.05), np.array([0.0, 0.0, -1.0])), rb + 0.05,
                         rel_tol=1e-12)
     # placed by a frame (quarter turn about x, scale 2): the ring's axis is
     # world y, so a ray down world y through the hole meets nothing
