@@ -552,6 +552,11 @@ int build_plan(smcrt_ctx *ctx, const smcrt_scene *sc, const smcrt_source *src, c
         for (int i = 0; i < np; ++i) plain = plain && plain_prim(sc->prims[i]);
         H.analytic_nrm = longest <= kAnalyticNormalMaxInstr && plain ? 1 : 0;
     }
+    // The plain mixed instantiation leaves the six-probe normal out of its
+    // loop (smaller loop: 4.6 % on the layered slab); a mixed scene whose
+    // normals need the probes runs the general one, whose plain-shape
+    // arithmetic is the same.
+    if (precision == SMCRT_MIXED && !H.analytic_nrm) H.general = 1;
     H.delta32 = std::max((float)sc->delta, 64.f * ulp_f32(rmax));
     H.h32 = 32.f * H.delta32;
     H.max_steps = sc->max_steps;

@@ -636,7 +636,7 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
         const float sg = cdot > 0.f ? 1.f : -1.f;
         float ex = px, ey = py, ez = pz;
         int sel = -2;
-        if (SMCRT_RARE(phase == kNrm)) {
+        if (G && SMCRT_RARE(phase == kNrm)) {   // probe normals: general instantiation only
             const float hh = (sub & 1) ? -hstep : hstep;
             const int a = sub >> 1;
             if (a == 0) ex = px + hh; else if (a == 1) ey = py + hh; else ez = pz + hh;
@@ -680,7 +680,7 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                     if (SMCRT_RARE(E.dmin < delta)) {
                         istar = E.istar;
                         dstar = E.dstar;
-                        if (S.analytic_nrm) {              // gradient of a short program, now
+                        if (!G || S.analytic_nrm) {        // gradient of a short program, now
                             grad_surface32(S, istar, px, py, pz, nx, ny, nz);
                             nrm_ready = true;
                         } else {                           // six probes in the next iterations
@@ -693,7 +693,7 @@ __device__ bool run_job_mixed(JobSlot *slots, JobWork *jobs, int njobs, int firs
                         seg_step = S.stepping == SMCRT_STEP_SEGMENT;
                     }
                 }
-            } else if (SMCRT_RARE(phase == kNrm)) {
+            } else if (G && SMCRT_RARE(phase == kNrm)) {
                 const float f = E.dsel;
                 if ((sub & 1) == 0) {
                     fplus = f;

@@ -239,6 +239,9 @@ int build_image(const smcrt_scene *sc, const smcrt_source *src, const smcrt_grid
         if (!plain) longest = kAnalyticNormalMaxInstr + 1;   // probe normals for other shapes and frames
         H.analytic_nrm = longest <= kAnalyticNormalMaxInstr ? 1 : 0;
     }
+    // probe normals run in the general mixed instantiation (the plain one
+    // leaves them out)
+    if (precision == SMCRT_MIXED && !H.analytic_nrm) H.general = 1;
     H.delta32 = std::fmax((float)sc->delta, 64.f * ulp32(rmax));
     H.h32 = 32.f * H.delta32;
     H.max_steps = sc->max_steps;
@@ -310,11 +313,15 @@ extern "C" int smcrt_run_noalloc(const smcrt_scene *scene, const smcrt_source *s
     int rc = scratch_address(&base);
     if (rc != SMCRT_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    // tori, cylinders, frames (and, in mixed precision, probe normals): the
+    // general instantiation, as the image's scene header records
+    bool general = false;
     {
         std::lock_guard<std::mutex> lk(g_image_mu);
         size_t used = 0;
         rc = build_image(scene, source, grid, precision, base, g_image, &used);
         if (rc != SMCRT_OK) return rc;
+        general = reinterpret_cast<const DevScene *>(g_image)->general != 0;
         if (npackets == 0) return SMCRT_OK;
         // the image (a multiple of 16 bytes), chunk by chunk, in the copy
         // kernels' launch arguments
@@ -344,8 +351,6 @@ extern "C" int smcrt_run_noalloc(const smcrt_scene *scene, const smcrt_source *s
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SMCRT_ERR_CUDA;
     const int threads = 128;
-    bool general = false;   // tori, cylinders, frames: the general-shape instantiation
-    for (int i = 0; i < scene->nprims; ++i) general = general || !plain_prim(scene->prims[i]);
     const int variant = (precision == SMCRT_FP64 ? 1 : 0) + (general ? kNumVariants : 0);
     const int occ = precision == SMCRT_FP64 ? occupancy_fp64(threads, variant) : occupancy_mixed(threads, variant);
     const int blocks = sms * (occ > 0 ? occ : 1);
